@@ -1,0 +1,109 @@
+"""Brute-force dense system matrix and dense restatements — test infrastructure only.
+
+The dense matrix is built by clipping every ray against every voxel box separately
+(slab method, vectorised over voxels). It is an algorithm independent of the Siddon
+trace in oracle.c, so A @ f vs the oracle's P f pins the projector on small grids.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _view_frame(geom, theta):
+    c, s = np.cos(theta), np.sin(theta)
+    S = np.array([geom.sad * c, geom.sad * s, 0.0])
+    C = np.array([-(geom.sdd - geom.sad) * c, -(geom.sdd - geom.sad) * s, 0.0])
+    eu = np.array([-s, c, 0.0])
+    ev = np.array([0.0, 0.0, 1.0])
+    return S, C, eu, ev
+
+
+def system_matrix(geom) -> np.ndarray:
+    """Dense A (M x N): A[i, j] = length (mm) of ray i (source to pixel centre) inside
+    the half-open voxel box j. Rows ordered (k, iv, iu), columns (iz, iy, ix)."""
+    n = np.array([geom.nx, geom.ny, geom.nz])
+    h = np.array([geom.dx, geom.dy, geom.dz])
+    o = -0.5 * n * h
+    lo_axes = [o[a] + np.arange(n[a]) * h[a] for a in range(3)]
+    hi_axes = [lo + h[a] for a, lo in enumerate(lo_axes)]
+    M = geom.n_views * geom.nv * geom.nu
+    N = geom.nx * geom.ny * geom.nz
+    A = np.zeros((M, N))
+    angles = geom.view_angles()
+    row = 0
+    for k in range(geom.n_views):
+        S, C, eu, ev = _view_frame(geom, angles[k])
+        for iv in range(geom.nv):
+            for iu in range(geom.nu):
+                u = geom.u_off + (iu - 0.5 * (geom.nu - 1)) * geom.du
+                v = geom.v_off + (iv - 0.5 * (geom.nv - 1)) * geom.dv
+                D = C + u * eu + v * ev
+                d = D - S
+                amin = [None] * 3
+                amax = [None] * 3
+                for a in range(3):
+                    if d[a] != 0.0:
+                        a0 = (lo_axes[a] - S[a]) / d[a]
+                        a1 = (hi_axes[a] - S[a]) / d[a]
+                        amin[a] = np.minimum(a0, a1)
+                        amax[a] = np.maximum(a0, a1)
+                    else:
+                        inside = (S[a] >= lo_axes[a]) & (S[a] < hi_axes[a])
+                        amin[a] = np.where(inside, -np.inf, np.inf)
+                        amax[a] = np.where(inside, np.inf, -np.inf)
+                lo3 = np.maximum(np.maximum(amin[2][:, None, None], amin[1][None, :, None]),
+                                 amin[0][None, None, :])
+                hi3 = np.minimum(np.minimum(amax[2][:, None, None], amax[1][None, :, None]),
+                                 amax[0][None, None, :])
+                lo3 = np.maximum(lo3, 0.0)
+                hi3 = np.minimum(hi3, 1.0)
+                A[row] = (np.maximum(hi3 - lo3, 0.0) * np.linalg.norm(d)).ravel()
+                row += 1
+    return A
+
+
+def cgls_dense(A, y, x0, n_iter):
+    """Appendix 1 CGLS on a dense matrix (the same listing, numpy vectors)."""
+    x = x0.astype(np.float64).copy()
+    r = y - A @ x
+    s = A.T @ r
+    p = s.copy()
+    gamma = s @ s
+    for _ in range(n_iter):
+        q = A @ p
+        delta = q @ q
+        if gamma == 0.0 or delta == 0.0:
+            break
+        alpha = gamma / delta
+        x += alpha * p
+        r -= alpha * q
+        s = A.T @ r
+        gnew = s @ s
+        p = s + (gnew / gamma) * p
+        gamma = gnew
+    return x
+
+
+def krylov_lsq(A, y, x0, n_iter):
+    """Minimiser of ||A x - y|| over x0 + span{s, (A^T A) s, ..., (A^T A)^(n-1) s},
+    s = A^T (y - A x0): what n CGLS steps compute in exact arithmetic. Solved by
+    least squares on an orthonormalised Krylov basis."""
+    r0 = y - A @ x0
+    s = A.T @ r0
+    B = A.T @ A
+    vecs = []
+    v = s.copy()
+    for _ in range(n_iter):
+        for w in vecs:  # modified Gram-Schmidt keeps the basis well conditioned
+            v = v - (w @ v) * w
+        nv = np.linalg.norm(v)
+        if nv < 1e-14 * max(1.0, np.linalg.norm(s)):
+            break
+        v = v / nv
+        vecs.append(v)
+        v = B @ v
+    if not vecs:
+        return x0.copy()
+    K = np.stack(vecs, axis=1)
+    c, *_ = np.linalg.lstsq(A @ K, r0, rcond=None)
+    return x0 + K @ c
