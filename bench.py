@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark of the tight-frame CBCT reconstruction hot path on GB300.
+
+One step = one full reconstruction of the paper-scale workload through the C ABI:
+512x512x70 voxels of 0.5x0.5x2.5 mm, 512x384 imager at 0.776 mm, 40 views (or --views 80),
+3-level multigrid (128x128x18 -> 256x256x35 -> 512x512x70), 50 A2 iterations split 8/17/25
+coarsest first (the paper's 1:2:3 proportions), 3 CGLS updates per iteration, mu = 5e-4,
+on a seeded 30-ellipsoid torso phantom with Poisson noise at 5e4 photons per ray.
+
+Metric: ray-voxel updates per second of P and P^T — the non-zeros of P (counted by the
+projector itself on every level) times the number of P and P^T applications a
+reconstruction performs (4 P and 3 P^T per A2 iteration), divided by the device time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--views 40|80] [--impl ours|reference]
+
+With --gpus N > 1 (launched by torch.distributed.run, one process per GPU) every rank
+reconstructs its own phantom (independent problems, weak scaling); there is no data
+exchange, only a host-side barrier and a max over ranks of the timed duration.
+--impl reference times the FP64 CPU oracle on a bounded sample (a few views of the same
+workload) in the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "ray-voxel updates/s (P+Pᵀ)"
+UNIT = "updates/s"
+MU = 5e-4
+N_CGLS = 3
+LEVELS = 3
+TOTAL_ITERS = 50
+PHOTONS = 5e4
+# FP32 arithmetic operations counted per ray-voxel update (roofline numerator): next
+# plane-crossing parameter (FMA), nearest crossing (min), segment length (subtract),
+# accumulation (FMA).
+OPS_PER_UPDATE = 4
+FP32_LANES_PER_SM = 128
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--views", type=int, default=40, choices=(40, 80))
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-views", type=int, default=8, help="views in the oracle's bounded sample")
+    return ap.parse_args(argv)
+
+
+def workload(views: int):
+    geom = synth.config_paper(views)
+    iters = synth.default_level_iters(LEVELS, TOTAL_ITERS)
+    return geom, iters
+
+
+def workload_config(geom, iters, extra=None):
+    cfg = {
+        "workload": (f"paper-scale TF-regularised CBCT reconstruction: {geom.nx}x{geom.ny}x{geom.nz} voxels "
+                     f"({geom.dx}x{geom.dy}x{geom.dz} mm), {geom.nu}x{geom.nv} imager at {geom.du} mm, "
+                     f"{geom.n_views} views, {LEVELS}-level multigrid, A2 iterations {iters} coarsest first, "
+                     f"{N_CGLS} CGLS updates each, mu={MU}"),
+        "volume": [geom.nx, geom.ny, geom.nz],
+        "views": geom.n_views,
+        "imager": [geom.nu, geom.nv],
+        "levels": LEVELS,
+        "iters_per_level": iters,
+        "n_cgls": N_CGLS,
+        "l2": "working set per step ~2.5 GB (> 126 MB L2); L2 also flushed (1 GiB write) before every timed step",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------------------------------
+# Distributed plumbing (host-side only: timing scalars, no data exchange)
+# ---------------------------------------------------------------------------------------
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group("gloo")
+    return dist
+
+
+def aggregate(local_seconds: float, local_units: float, dist=None):
+    """Whole-job numbers: max over ranks of the timed duration, sum over ranks of the work."""
+    if dist is None:
+        return local_seconds, local_units
+    import torch
+    t = torch.tensor([local_seconds], dtype=torch.float64)
+    u = torch.tensor([local_units], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+# ---------------------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the workload
+# ---------------------------------------------------------------------------------------
+
+def oracle_sample(geom, n_views: int, seed: int):
+    """P + P^T of the oracle on the first n_views views; returns (updates, seconds, cores)."""
+    import dataclasses
+    import oracle
+    sub = dataclasses.replace(geom, n_views=n_views, angles=tuple(geom.view_angles()[:n_views]))
+    f = synth.voxelize(sub, synth.torso_ellipsoids(sub, 1002))
+    y = synth.random_projections(sub, seed)
+    nnz = oracle.count_nnz(sub)
+    t0 = time.perf_counter()
+    oracle.project(sub, f)
+    oracle.backproject(sub, y)
+    dt = time.perf_counter() - t0
+    return 2 * nnz, dt, oracle.num_threads()
+
+
+def run_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    geom, iters = workload(args.views)
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle_sample(geom, 1, 7)
+    upd, secs, cores = 0.0, 0.0, oracle.num_threads()
+    for k in range(args.steps):
+        u, s, cores = oracle_sample(geom, args.cpu_views, 100 + k)
+        upd += u
+        secs += s
+    value = upd / secs
+    sample = f"P + P^T of {args.cpu_views} of the {geom.n_views} views per step (nnz counted by the oracle)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic torso phantom (30 ellipsoids), uniform random projections",
+        "config": workload_config(geom, iters, {"sample": sample}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+# The CUDA path
+# ---------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_info()
+    dist = dist_init(world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1008_2042_gb300 import build as cuda_build
+    cuda_build.build()
+    import paper_1008_2042_gb300 as cb
+
+    geom, iters = workload(args.views)
+    g = cb.Geometry(geom)
+    # input: seeded torso phantom, projected with the library's projector, Poisson noise
+    f_true = torch.tensor(synth.voxelize(geom, synth.torso_ellipsoids(geom, 1002)), dtype=torch.float32, device=dev)
+    p_ideal = cb.project(g, f_true).double().cpu().numpy()
+    y_host = torch.tensor(synth.noisy_line_integrals(p_ideal, PHOTONS, 2002 + rank), dtype=torch.float32).pin_memory()
+    y = y_host.to(dev)
+    nnz = [cb.count_nnz(g, lev) for lev in range(LEVELS)]  # level 0 = finest
+    p_per_iter, pt_per_iter = N_CGLS + 1, N_CGLS
+    updates_P = sum(iters[LEVELS - 1 - lev] * p_per_iter * nnz[lev] for lev in range(LEVELS))
+    updates_PT = sum(iters[LEVELS - 1 - lev] * pt_per_iter * nnz[lev] for lev in range(LEVELS))
+    updates = updates_P + updates_PT
+
+    ws = torch.empty(cb.reconstruct_workspace_size(g), dtype=torch.uint8, device=dev)
+    out = torch.empty(geom.vol_shape, dtype=torch.float32, device=dev)
+    flush = torch.empty(1 << 28, dtype=torch.float32, device=dev)  # 1 GiB
+    stream = torch.cuda.current_stream()
+
+    def step(y_in, o):
+        cb.reconstruct(g, y_in, MU, LEVELS, iters, n_cgls=N_CGLS, workspace=ws, out=o)
+
+    for _ in range(max(args.warmup, 0)):
+        step(y, out)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs resident in HBM ----
+    gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid) if hasattr(
+        torch.cuda.get_device_properties(local), "uuid") else str(local)
+    sampler = ClockSampler(gpu_id)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    cb.profiling_reset()
+    cb.profiling(True)
+    launches0 = cb.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        step(y, out)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = cb.launch_count() - launches0
+    cb.profiling(False)
+    ktimes = cb.kernel_times()
+    clocks = sampler.stop()
+    if dist is not None:
+        dist.barrier()
+    local_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    secs, total_updates = aggregate(local_s, updates * args.steps, dist)
+    value = total_updates / secs
+
+    # ---- end to end through the public API: host buffers, copies inside the timed region ----
+    out_host = torch.empty(geom.vol_shape, dtype=torch.float32).pin_memory()
+    y_dev = torch.empty_like(y)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        y_dev.copy_(y_host, non_blocking=True)
+        step(y_dev, out)
+        out_host.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s, _ = aggregate(e0.elapsed_time(e1) / 1e3, 0.0, dist)
+    e2e_value = total_updates / e2e_s
+
+    # ---- roofline of the dominant kernel (P or P^T), from the live event timings ----
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
+    alu_peak = sms * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12  # T FP32 ops/s (one per lane per clock)
+    ms_p, n_p = ktimes["project"]
+    ms_pt, n_pt = ktimes["backproject"]
+    if ms_p >= ms_pt:
+        dom, ms_dom, n_dom, upd_dom = "project (P, Siddon column sweep)", ms_p, n_p, updates_P * args.steps
+    else:
+        dom, ms_dom, n_dom, upd_dom = "backproject (exact P^T gather)", ms_pt, n_pt, updates_PT * args.steps
+    achieved = (upd_dom * OPS_PER_UPDATE / max(n_dom, 1)) / (ms_dom / max(n_dom, 1) / 1e3) / 1e12
+    total_kernel_ms = sum(v[0] for v in ktimes.values())
+    roofline = {
+        "bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+        "frac": achieved / alu_peak, "traffic": None,
+        "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz (one FP32 op per lane "
+                       f"per clock; {OPS_PER_UPDATE} FP32 ops counted per ray-voxel update)",
+        "avg_launch_ms": ms_dom / max(n_dom, 1),
+        "kernel_share": {k: round(v[0] / total_kernel_ms, 4) for k, v in ktimes.items()} if total_kernel_ms else {},
+        "hbm_compulsory_gbs": None,
+    }
+    # compulsory DRAM bytes of P at the finest level: read the volume, write the stack
+    n0 = geom.nx * geom.ny * geom.nz
+    m0 = geom.n_views * geom.nv * geom.nu
+    roofline["hbm_compulsory_gbs"] = 4.0 * (n0 + m0) / (ms_dom / max(n_dom, 1) / 1e3) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            u, s, cores = oracle_sample(geom, args.cpu_views, 3003)
+            cpu = {"value": u / s, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"P + P^T of {args.cpu_views} of the {geom.n_views} views of the same workload "
+                             f"({s:.1f} s)"}
+        except Exception as exc:  # the oracle is a reported baseline only
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {exc}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: seeded 30-ellipsoid torso phantom, Poisson noise 5e4 photons/ray (per-rank seeds)",
+            "config": workload_config(geom, iters, {"nnz_per_P": nnz,
+                                                    "updates_per_step": updates,
+                                                    "recon_seconds": secs / args.steps,
+                                                    "parallelism": f"replicas x{world}"}),
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(y_host.numel() * 4),
+                    "d2h_bytes_per_step": int(out_host.numel() * 4),
+                    "ms_per_step": 1e3 * e2e_s / args.steps},
+            "gpu_launches": int(launches),
+            "roofline": roofline,
+            "kernel_ms": {k: v[0] for k, v in ktimes.items()},
+            "kernel_launches": {k: v[1] for k, v in ktimes.items()},
+            "clocks": clocks,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    g.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

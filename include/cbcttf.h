@@ -1,0 +1,236 @@
+/*
+ * cbcttf — tight-frame regularised cone-beam CT reconstruction on one GPU (sm_103a).
+ *
+ * C ABI of the CUDA library. It implements the hot path of Jia, Dong, Lou and Jiang,
+ * "GPU-based iterative cone beam CT reconstruction using tight frame regularization":
+ * the Siddon forward projector P, its exact adjoint P^T, the piecewise-linear tight-frame
+ * analysis W (the paper's D) and synthesis W^T with vector soft-thresholding T_mu and the
+ * positivity correction H, CGLS, Algorithm A2 and the coarse-to-fine multigrid.
+ *
+ * Conventions shared by every call
+ *   - Volumes are float32, layout [nz][ny][nx] (x fastest). Voxel (ix, iy, iz) is the
+ *     half-open box [x0 + ix dx, x0 + (ix+1) dx) x ..., with x0 = -nx dx / 2 (the volume
+ *     is centred on the rotation axis z); the same for y and z.
+ *   - Projection stacks are float32, layout [n_views][nv][nu] (u fastest).
+ *   - Tight-frame coefficients are float32, layout [27][nz][ny][nx]; channel
+ *     i = l + 3 m + 9 n holds the filter h_l along x, h_m along y and h_n along z.
+ *   - Geometry (Section 2.1, Fig. 1): view k at angle t_k puts the source at
+ *     sad (cos t, sin t, 0) and the imager centre at -(sdd - sad)(cos t, sin t, 0); the
+ *     imager u axis is (-sin t, cos t, 0), its v axis is z. Pixel (iu, iv) is centred at
+ *     u = u_off + (iu - (nu-1)/2) du, v = v_off + (iv - (nv-1)/2) dv. One ray per pixel
+ *     centre. Lengths in mm, attenuation in 1/mm, angles in radians.
+ *   - Data pointers are DEVICE pointers on the device that was current when the geometry
+ *     was created, owned by the caller, never retained after the call returns. Outputs
+ *     are overwritten (not accumulated). Input and output buffers must not overlap.
+ *   - Every call is enqueued on `stream` (NULL = the legacy default stream) and returns
+ *     without waiting, except where stated. Arguments are validated before anything is
+ *     launched; an invalid call launches nothing and returns CBCT_ERR_INVALID_ARG.
+ *   - Errors are returned as cbct_status; cbct_last_error() gives a message for the
+ *     calling thread. No C++ exception crosses this interface.
+ *   - A geometry handle is not thread-safe: calls sharing one handle must not run
+ *     concurrently from several host threads (they share the handle's device scratch).
+ */
+#ifndef CBCTTF_H
+#define CBCTTF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *cbct_stream_t;
+
+typedef enum {
+    CBCT_OK = 0,
+    CBCT_ERR_INVALID_ARG = 1,   /* null pointer, non-positive size, inconsistent geometry */
+    CBCT_ERR_OUT_OF_MEMORY = 2, /* device allocation failed, or the workspace is too small */
+    CBCT_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
+    CBCT_ERR_NONFINITE = 4,     /* an inner product of the iteration was NaN or Inf */
+    CBCT_ERR_UNSUPPORTED = 5    /* a parameter the method does not define (e.g. lambda != 0) */
+} cbct_status;
+
+/* Scan geometry (Section 2.1, Fig. 1; Section 3 gives sad = 1000 mm, sdd = 1500 mm). */
+typedef struct {
+    int nx, ny, nz;          /* voxels per axis, >= 1 */
+    double dx, dy, dz;       /* voxel size (mm), > 0 */
+    int nu, nv;              /* imager pixels, >= 1, nv <= 8192 */
+    double du, dv;           /* pixel pitch (mm), > 0 */
+    double u_off, v_off;     /* imager offset from the central ray (mm) */
+    double sad, sdd;         /* source-to-axis and source-to-imager distance (mm) */
+    int n_views;             /* number of views, >= 1 */
+    const double *angles;    /* host array of n_views angles (rad); NULL = 2 pi k / n_views */
+} cbct_geometry_desc;
+
+/* Opaque, library-owned geometry: per-view tables and device scratch. */
+typedef struct cbct_geometry cbct_geometry;
+
+/* Options of the outer iteration. */
+typedef struct {
+    int n_cgls;     /* CGLS updates per outer iteration (Appendix 1: "M = 2~3"); default 3 */
+    int momentum;   /* 1 = Algorithm A2 (default), 0 = Algorithm A1 */
+    int positivity; /* 1 = apply H after the shrinkage (default), 0 = skip H */
+} cbct_recon_opts;
+
+/*
+ * Creates a geometry on the current CUDA device and copies the view table to it.
+ * The whole volume must lie strictly between the source and the imager for every view
+ * (its transverse half-diagonal below both sad and sdd - sad). Sizes are limited to
+ * nx, ny, nz <= 65535, nx*ny*nz < 2^31 voxels and n_views*nv*nu < 2^31 pixels.
+ * Synchronous. Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA.
+ */
+cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct_geometry **out);
+
+/* Frees the geometry and its device scratch (waits for the device). NULL is a no-op. */
+cbct_status cbct_geometry_destroy(cbct_geometry *geom);
+
+/*
+ * Forward projection g = P f (Eq. (1); Section 2.2.1: one ray per pixel, Siddon's exact
+ * ray tracing): g_i = sum_j a_ij f_j, a_ij = length (mm) of ray i inside voxel j.
+ * f: device [nz][ny][nx]; g: device [n_views][nv][nu]. FP32 arithmetic.
+ * Uses the geometry's scratch (allocated on first use: one volume).
+ */
+cbct_status cbct_project(const cbct_geometry *geom, const float *f, float *g,
+                         cbct_stream_t stream);
+
+/*
+ * Exact adjoint f = P^T g: f_j = sum_i a_ij g_i with the same a_ij as cbct_project, so
+ * <P f, g> = <f, P^T g> (Eq. (A1)). Computed by gathering per voxel (no atomics; the
+ * result does not depend on scheduling). The paper's own backprojector (Eq. (3)) is an
+ * approximation of this operator and is not what this call computes.
+ * g: device [n_views][nv][nu]; f: device [nz][ny][nx]. FP32 arithmetic.
+ * Uses the geometry's scratch (allocated on first use: one projection stack).
+ */
+cbct_status cbct_backproject(const cbct_geometry *geom, const float *g, float *f,
+                             cbct_stream_t stream);
+
+/*
+ * Tight-frame analysis alpha = W f (Section 2.1): alpha_i(x) = sum_k psi_i(k) f(x - k),
+ * psi_i(k) = h_l(k_x) h_m(k_y) h_n(k_z) with h_0 = [1,2,1]/4, h_1 = sqrt(2)/4 [1,0,-1],
+ * h_2 = [-1,2,-1]/4 (taps at offsets -1, 0, +1). The volume is periodic along every
+ * axis, which makes W^T W = I exact.
+ * f: device [nz][ny][nx]; alpha27: device [27][nz][ny][nx].
+ */
+cbct_status cbct_tf_analyze(int nx, int ny, int nz, const float *f, float *alpha27,
+                            cbct_stream_t stream);
+
+/*
+ * Shrinkage and synthesis f = H(W^T T_mu alpha) (Eq. (2) and Section 2.1): at every
+ * voxel the 26 high-pass coefficients are scaled by max(1 - mu / ||alpha_h||, 0) (0 when
+ * the norm is 0), alpha_0 is kept, then f(x) = sum_i sum_k psi_i(k) alpha_i(x + k)
+ * (periodic); negative voxels are set to 0 if positivity != 0. mu >= 0.
+ * alpha27: device [27][nz][ny][nx] (not modified); f: device [nz][ny][nx].
+ */
+cbct_status cbct_tf_synthesize_shrink(int nx, int ny, int nz, const float *alpha27,
+                                      float mu, int positivity, float *f,
+                                      cbct_stream_t stream);
+
+/*
+ * CGLS (Appendix 1): n_iter updates of x for min ||P x - y||^2 starting from x.
+ * Inner products are accumulated in FP64 on the device; if ||P^T r||^2 or ||P p||^2
+ * becomes zero the remaining updates leave x unchanged.
+ * y: device [n_views][nv][nu]; x: device [nz][ny][nx], read and overwritten.
+ * Uses the geometry's reconstruction workspace (allocated on first use).
+ * Synchronises the stream to check for non-finite inner products (NONFINITE).
+ */
+cbct_status cbct_cgls(const cbct_geometry *geom, const float *y, float *x, int n_iter,
+                      cbct_stream_t stream);
+
+/*
+ * Reconstruction (Section 2.2.3 multigrid around Algorithm A2 of Section 2.1):
+ * `levels` grids, level l having ceil(n / 2^l) voxels per axis at 2^l times the voxel
+ * size with the same centre; the imager and y are used unchanged on every level.
+ * Starts from f = 0 on the coarsest grid, runs iters[levels-1-l] A2 iterations on
+ * level l (iters is listed coarsest first), and prolongs each level's result by
+ * trilinear interpolation as the next finer level's initial guess. Each A2 iteration
+ * does n_cgls CGLS updates from the momentum point v, then f = H(W^T T_mu W x).
+ * mu >= 0 is the threshold of Eq. (2), the method's only tuning parameter (Section 2.1);
+ * lambda must be 0 (UNSUPPORTED otherwise: the method has no second parameter).
+ * y: device [n_views][nv][nu]; f_out: device [nz][ny][nx] (finest grid).
+ * Uses the geometry's reconstruction workspace (allocated on first use; its size is
+ * cbct_reconstruct_workspace_size). Synchronises the stream at the end.
+ * Errors: INVALID_ARG, UNSUPPORTED, OUT_OF_MEMORY, CUDA, NONFINITE.
+ */
+cbct_status cbct_reconstruct(const float *y, const cbct_geometry *geom, float mu,
+                             float lambda, int levels, const int *iters, float *f_out,
+                             cbct_stream_t stream);
+
+/*
+ * As cbct_reconstruct with options (NULL = defaults) and a caller-provided device
+ * workspace of at least cbct_reconstruct_workspace_size bytes (NULL = the geometry's
+ * own workspace). The workspace must not be used by anything else while the call's
+ * work is on the device.
+ */
+cbct_status cbct_reconstruct_ex(const float *y, const cbct_geometry *geom, float mu,
+                                float lambda, int levels, const int *iters,
+                                const cbct_recon_opts *opts, void *workspace,
+                                size_t workspace_bytes, float *f_out, cbct_stream_t stream);
+
+/* Bytes of device workspace cbct_reconstruct_ex needs for this geometry (any levels). */
+cbct_status cbct_reconstruct_workspace_size(const cbct_geometry *geom, size_t *bytes);
+
+/*
+ * Trilinear prolongation between multigrid levels (Section 2.2.3, "linear
+ * interpolation"): every fine voxel centre is interpolated from the coarse grid, both
+ * grids centred on the origin, coarse coordinates clamped to the hull of coarse voxel
+ * centres. fc: device [cnz][cny][cnx]; ff: device [nz][ny][nx].
+ */
+cbct_status cbct_prolong(int cnx, int cny, int cnz, double cdx, double cdy, double cdz,
+                         const float *fc, int nx, int ny, int nz, double dx, double dy,
+                         double dz, float *ff, cbct_stream_t stream);
+
+/*
+ * Restriction, the counterpart of cbct_prolong (not used by the coarse-to-fine scheme
+ * of Section 2.2.3): each coarse voxel is the mean of the fine voxels whose centres lie
+ * inside it (0 if there are none). ff: device [nz][ny][nx]; fc: device [cnz][cny][cnx].
+ */
+cbct_status cbct_restrict(int nx, int ny, int nz, double dx, double dy, double dz,
+                          const float *ff, int cnx, int cny, int cnz, double cdx,
+                          double cdy, double cdz, float *fc, cbct_stream_t stream);
+
+/*
+ * Number of non-zeros of P on multigrid level `level` (0 = the geometry's own grid):
+ * the (ray, voxel) pairs whose segment is longer than 1e-3 of the smallest voxel side,
+ * counted by the projector's own traversal. This is the work unit of the ray-voxel
+ * update rate (Section 2.2.2 quotes about 4e9 for a clinical case). Synchronous.
+ */
+cbct_status cbct_count_nnz(const cbct_geometry *geom, int level, unsigned long long *nnz,
+                           cbct_stream_t stream);
+
+/* Kernel families reported by cbct_kernel_time. */
+typedef enum {
+    CBCT_KERNEL_PROJECT = 0,     /* the projector P */
+    CBCT_KERNEL_BACKPROJECT = 1, /* the adjoint P^T */
+    CBCT_KERNEL_TF_ANALYZE = 2,  /* W */
+    CBCT_KERNEL_TF_SYNTH = 3,    /* T_mu, W^T, H */
+    CBCT_KERNEL_OTHER = 4,       /* vector updates, reductions, transfers, layout changes */
+    CBCT_KERNEL_KINDS = 5
+} cbct_kernel_kind;
+
+/*
+ * Measurement support (not part of the paper's method). While enabled, every kernel the
+ * library launches is bracketed by two CUDA events recorded on the launching stream;
+ * cbct_kernel_time waits for the recorded events and returns, per family, the summed
+ * device time and the number of launches since the last reset. Process-wide; enabling
+ * adds two event records per launch.
+ */
+cbct_status cbct_profiling_enable(int enable);
+cbct_status cbct_profiling_reset(void);
+cbct_status cbct_kernel_time(int kind, double *total_ms, unsigned long long *launches);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *cbct_last_error(void);
+
+/* Number of kernels this library has launched in this process (all threads). */
+unsigned long long cbct_launch_count(void);
+
+/* Library version string. */
+const char *cbct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CBCTTF_H */

@@ -1,0 +1,312 @@
+"""Python binding of the cbcttf C ABI (include/cbcttf.h).
+
+Argument marshalling only: every step runs in the CUDA library ``libcbcttf.so``, built
+in-tree by ``paper_1008_2042_gb300.build.build()``. PyTorch supplies device memory and
+the current stream. There is no CPU fallback: if the library is missing or no GPU is
+present, calls raise.
+
+Layouts follow the C ABI: volumes (nz, ny, nx) float32, projection stacks
+(n_views, nv, nu) float32, frame coefficients (27, nz, ny, nx) float32, all contiguous
+CUDA tensors on the device the geometry was created on.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcbcttf.so")
+
+_lib = None
+
+
+class CbctError(RuntimeError):
+    """A non-OK status returned by the library."""
+
+    def __init__(self, status: int, message: str):
+        super().__init__(f"cbcttf status {status}: {message}")
+        self.status = status
+
+
+class GeometryDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("nu", ctypes.c_int), ("nv", ctypes.c_int),
+                ("du", ctypes.c_double), ("dv", ctypes.c_double),
+                ("u_off", ctypes.c_double), ("v_off", ctypes.c_double),
+                ("sad", ctypes.c_double), ("sdd", ctypes.c_double),
+                ("n_views", ctypes.c_int), ("angles", ctypes.POINTER(ctypes.c_double))]
+
+
+class ReconOpts(ctypes.Structure):
+    _fields_ = [("n_cgls", ctypes.c_int), ("momentum", ctypes.c_int), ("positivity", ctypes.c_int)]
+
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+_f = ctypes.c_float
+
+_SIGNATURES = {
+    "cbct_geometry_create": [ctypes.POINTER(GeometryDesc), ctypes.POINTER(_vp)],
+    "cbct_geometry_destroy": [_vp],
+    "cbct_project": [_vp, _vp, _vp, _vp],
+    "cbct_backproject": [_vp, _vp, _vp, _vp],
+    "cbct_tf_analyze": [_i, _i, _i, _vp, _vp, _vp],
+    "cbct_tf_synthesize_shrink": [_i, _i, _i, _vp, _f, _i, _vp, _vp],
+    "cbct_cgls": [_vp, _vp, _vp, _i, _vp],
+    "cbct_reconstruct": [_vp, _vp, _f, _f, _i, ctypes.POINTER(_i), _vp, _vp],
+    "cbct_reconstruct_ex": [_vp, _vp, _f, _f, _i, ctypes.POINTER(_i), ctypes.POINTER(ReconOpts),
+                            _vp, ctypes.c_size_t, _vp, _vp],
+    "cbct_reconstruct_workspace_size": [_vp, ctypes.POINTER(ctypes.c_size_t)],
+    "cbct_prolong": [_i, _i, _i, _d, _d, _d, _vp, _i, _i, _i, _d, _d, _d, _vp, _vp],
+    "cbct_restrict": [_i, _i, _i, _d, _d, _d, _vp, _i, _i, _i, _d, _d, _d, _vp, _vp],
+    "cbct_count_nnz": [_vp, _i, ctypes.POINTER(ctypes.c_ulonglong), _vp],
+    "cbct_profiling_enable": [_i],
+    "cbct_profiling_reset": [],
+    "cbct_kernel_time": [_i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_ulonglong)],
+}
+
+KERNEL_KINDS = {"project": 0, "backproject": 1, "tf_analyze": 2, "tf_synth": 3, "other": 4}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libcbcttf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with paper_1008_2042_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        for name, args in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        lib.cbct_last_error.restype = ctypes.c_char_p
+        lib.cbct_last_error.argtypes = []
+        lib.cbct_version.restype = ctypes.c_char_p
+        lib.cbct_version.argtypes = []
+        lib.cbct_launch_count.restype = ctypes.c_ulonglong
+        lib.cbct_launch_count.argtypes = []
+        _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise CbctError(status, load_library().cbct_last_error().decode())
+
+
+def _stream(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, shape, name: str) -> ctypes.c_void_p:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load_library().cbct_launch_count())
+
+
+def version() -> str:
+    return load_library().cbct_version().decode()
+
+
+class Geometry:
+    """Owns a cbct_geometry handle. Accepts any object with the fields of
+    cbct_geometry_desc (nx, ny, nz, dx, dy, dz, nu, nv, du, dv, sad, sdd, n_views, and
+    optionally u_off, v_off, angles), or the same as keyword arguments."""
+
+    def __init__(self, desc=None, **kw):
+        lib = load_library()
+        get = (lambda k, d=None: getattr(desc, k, d)) if desc is not None else (lambda k, d=None: kw.get(k, d))
+        self.nx, self.ny, self.nz = int(get("nx")), int(get("ny")), int(get("nz"))
+        self.dx, self.dy, self.dz = float(get("dx")), float(get("dy")), float(get("dz"))
+        self.nu, self.nv = int(get("nu")), int(get("nv"))
+        self.du, self.dv = float(get("du")), float(get("dv"))
+        self.u_off, self.v_off = float(get("u_off", 0.0)), float(get("v_off", 0.0))
+        self.sad, self.sdd = float(get("sad", 1000.0)), float(get("sdd", 1500.0))
+        self.n_views = int(get("n_views"))
+        angles = get("angles", None)
+        self._angles = None
+        ap = None
+        if angles is not None:
+            self._angles = (ctypes.c_double * self.n_views)(*[float(a) for a in angles])
+            ap = ctypes.cast(self._angles, ctypes.POINTER(ctypes.c_double))
+        d = GeometryDesc(self.nx, self.ny, self.nz, self.dx, self.dy, self.dz, self.nu, self.nv,
+                         self.du, self.dv, self.u_off, self.v_off, self.sad, self.sdd,
+                         self.n_views, ap)
+        h = ctypes.c_void_p()
+        _check(lib.cbct_geometry_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.device = torch.cuda.current_device()
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def vol_shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def proj_shape(self):
+        return (self.n_views, self.nv, self.nu)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().cbct_geometry_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def project(geom: Geometry, f: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """g = P f (Siddon forward projection)."""
+    if out is None:
+        out = torch.empty(geom.proj_shape, dtype=torch.float32, device=f.device)
+    _check(load_library().cbct_project(geom.handle, _dev(f, geom.vol_shape, "f"),
+                                       _dev(out, geom.proj_shape, "out"), _stream(stream)))
+    return out
+
+
+def backproject(geom: Geometry, g: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """f = P^T g (exact adjoint)."""
+    if out is None:
+        out = torch.empty(geom.vol_shape, dtype=torch.float32, device=g.device)
+    _check(load_library().cbct_backproject(geom.handle, _dev(g, geom.proj_shape, "g"),
+                                           _dev(out, geom.vol_shape, "out"), _stream(stream)))
+    return out
+
+
+def tf_analyze(f: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """alpha = W f, 27 channels."""
+    nz, ny, nx = f.shape
+    if out is None:
+        out = torch.empty((27, nz, ny, nx), dtype=torch.float32, device=f.device)
+    _check(load_library().cbct_tf_analyze(nx, ny, nz, _dev(f, None, "f"),
+                                          _dev(out, (27, nz, ny, nx), "out"), _stream(stream)))
+    return out
+
+
+def tf_synthesize_shrink(alpha: torch.Tensor, mu: float, positivity: bool = True,
+                         out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """f = H(W^T T_mu alpha) (H only if positivity)."""
+    _, nz, ny, nx = alpha.shape
+    if out is None:
+        out = torch.empty((nz, ny, nx), dtype=torch.float32, device=alpha.device)
+    _check(load_library().cbct_tf_synthesize_shrink(nx, ny, nz, _dev(alpha, None, "alpha"), float(mu),
+                                                    int(bool(positivity)), _dev(out, (nz, ny, nx), "out"),
+                                                    _stream(stream)))
+    return out
+
+
+def cgls(geom: Geometry, y: torch.Tensor, x: torch.Tensor, n_iter: int, stream=None) -> torch.Tensor:
+    """n_iter CGLS updates of x in place (Appendix 1); returns x."""
+    _check(load_library().cbct_cgls(geom.handle, _dev(y, geom.proj_shape, "y"), _dev(x, geom.vol_shape, "x"),
+                                    int(n_iter), _stream(stream)))
+    return x
+
+
+def reconstruct(geom: Geometry, y: torch.Tensor, mu: float, levels: int, iters: Sequence[int],
+                lam: float = 0.0, n_cgls: int = 3, momentum: bool = True, positivity: bool = True,
+                workspace: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
+                stream=None) -> torch.Tensor:
+    """Multigrid A2 reconstruction; iters lists the outer iterations per level, coarsest first."""
+    lib = load_library()
+    if len(iters) != levels:
+        raise ValueError("iters must have one entry per level")
+    if out is None:
+        out = torch.empty(geom.vol_shape, dtype=torch.float32, device=y.device)
+    it = (ctypes.c_int * levels)(*[int(v) for v in iters])
+    opts = ReconOpts(int(n_cgls), int(bool(momentum)), int(bool(positivity)))
+    ws, ws_bytes = None, 0
+    if workspace is not None:
+        if not workspace.is_cuda or not workspace.is_contiguous():
+            raise TypeError("workspace must be a contiguous CUDA tensor")
+        ws = ctypes.c_void_p(workspace.data_ptr())
+        ws_bytes = workspace.numel() * workspace.element_size()
+    _check(lib.cbct_reconstruct_ex(_dev(y, geom.proj_shape, "y"), geom.handle, float(mu), float(lam), int(levels),
+                                   it, ctypes.byref(opts), ws, ctypes.c_size_t(ws_bytes),
+                                   _dev(out, geom.vol_shape, "out"), _stream(stream)))
+    return out
+
+
+def reconstruct_workspace_size(geom: Geometry) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().cbct_reconstruct_workspace_size(geom.handle, ctypes.byref(n)))
+    return int(n.value)
+
+
+def prolong(fc: torch.Tensor, coarse_spacing, fine_shape, fine_spacing, out=None, stream=None) -> torch.Tensor:
+    """Trilinear prolongation coarse (nz, ny, nx) -> fine grid, both centred on the origin."""
+    cnz, cny, cnx = fc.shape
+    nz, ny, nx = fine_shape
+    if out is None:
+        out = torch.empty((nz, ny, nx), dtype=torch.float32, device=fc.device)
+    cdx, cdy, cdz = coarse_spacing
+    dx, dy, dz = fine_spacing
+    _check(load_library().cbct_prolong(cnx, cny, cnz, cdx, cdy, cdz, _dev(fc, None, "fc"), nx, ny, nz, dx, dy, dz,
+                                       _dev(out, (nz, ny, nx), "out"), _stream(stream)))
+    return out
+
+
+def restrict(ff: torch.Tensor, fine_spacing, coarse_shape, coarse_spacing, out=None, stream=None) -> torch.Tensor:
+    """Mean of the fine voxels whose centres fall in each coarse voxel."""
+    nz, ny, nx = ff.shape
+    cnz, cny, cnx = coarse_shape
+    if out is None:
+        out = torch.empty((cnz, cny, cnx), dtype=torch.float32, device=ff.device)
+    dx, dy, dz = fine_spacing
+    cdx, cdy, cdz = coarse_spacing
+    _check(load_library().cbct_restrict(nx, ny, nz, dx, dy, dz, _dev(ff, None, "ff"), cnx, cny, cnz, cdx, cdy, cdz,
+                                        _dev(out, (cnz, cny, cnx), "out"), _stream(stream)))
+    return out
+
+
+def count_nnz(geom: Geometry, level: int = 0, stream=None) -> int:
+    """Non-zeros of P on a multigrid level, counted by the projector itself."""
+    n = ctypes.c_ulonglong()
+    _check(load_library().cbct_count_nnz(geom.handle, int(level), ctypes.byref(n), _stream(stream)))
+    return int(n.value)
+
+
+def profiling(enable: bool) -> None:
+    """Bracket every library kernel launch with CUDA events (measurement support)."""
+    _check(load_library().cbct_profiling_enable(int(bool(enable))))
+
+
+def profiling_reset() -> None:
+    _check(load_library().cbct_profiling_reset())
+
+
+def kernel_times() -> dict:
+    """Per kernel family: (summed device ms, launches) since the last reset."""
+    lib = load_library()
+    out = {}
+    for name, kind in KERNEL_KINDS.items():
+        ms, n = ctypes.c_double(), ctypes.c_ulonglong()
+        _check(lib.cbct_kernel_time(kind, ctypes.byref(ms), ctypes.byref(n)))
+        out[name] = (float(ms.value), int(n.value))
+    return out

@@ -1,0 +1,157 @@
+// Internal declarations of the cbcttf CUDA library (not part of the C ABI).
+//
+// Internal data layouts (the public ABI converts at its boundary):
+//   volumes inside the iteration are z-fastest, [ny][nx][nz], so that the projector's
+//   warps, whose lanes are adjacent imager rows, read adjacent z voxels of one (x, y)
+//   column; public volumes are x-fastest [nz][ny][nx]. Kernels that touch volumes take
+//   the element strides (sx, sy, sz) so they serve both layouts.
+//   projection stacks are always [n_views][nv][nu].
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/cbcttf.h"
+
+namespace cbct {
+
+// Geometry of one multigrid level as the kernels see it (FP32, derived from the FP64
+// description on the host). All rays of view k at imager column u share their
+// transverse (x, y) path; the v coordinate only tilts the ray in z (Section 2.1 geometry:
+// the source orbit lies in the plane z = 0 and the imager's v axis is z).
+struct GeomDev {
+    int nx, ny, nz;
+    float dx, dy, dz;
+    float x0, y0, z0;       // volume corner, -n * d / 2
+    int nu, nv, nviews;
+    float du, dv;
+    float u_first, v_first; // coordinates of pixel 0
+    float inv_du, inv_dv;
+    float sad, sdd;
+    float tc;               // sad / sdd: ray parameter of the isocentre plane
+    const float2 *cs;       // (cos t_k, sin t_k) per view, device memory
+};
+
+// Rays are parametrised as X(tau) = Q + tau * d, d = D - S (source to pixel centre) and
+// Q = S + tc * d, the point where the ray crosses the plane through the rotation axis
+// parallel to the imager. For the circular orbit Q = tc * (u e_u + v e_z), so Q and the
+// plane offsets stay small numbers and FP32 keeps ~1e-5 mm resolution along the ray.
+// tau runs from -tc (source) to 1 - tc (pixel); the volume lies strictly inside.
+
+// Coordinate of plane i of an axis with origin o and spacing h. P and P^T both use this
+// exact expression so that both compute bit-identical crossing parameters.
+__device__ __forceinline__ float plane_at(int i, float h, float o) { return fmaf((float)i, h, o); }
+
+// Transverse part of ray (view with cos/sin c, s; imager coordinate u).
+__device__ __forceinline__ void ray_xy(const GeomDev &G, float c, float s, float u, float &dxr,
+                                       float &dyr, float &qx, float &qy)
+{
+    dxr = fmaf(-u, s, -G.sdd * c);
+    dyr = fmaf(u, c, -G.sdd * s);
+    float tu = G.tc * u;
+    qx = -tu * s;
+    qy = tu * c;
+}
+
+// 1 / d with a finite stand-in for d == 0 (such a ray never crosses that plane family).
+__device__ __forceinline__ float safe_rcp(float d) { return d != 0.0f ? __frcp_rn(d) : 1e30f; }
+
+// tau at which a ray with transverse offset q and reciprocal direction inv crosses plane p.
+__device__ __forceinline__ float tau_plane(float p, float q, float inv) { return (p - q) * inv; }
+
+// tau at which the ray through imager row v (1/v = inv_v) crosses the plane z = p:
+// z(tau) = v (tc + tau) for every ray of the orbit, hence tau = p / v - tc.
+__device__ __forceinline__ float tau_zplane(float p, float inv_v, float tc) { return fmaf(p, inv_v, -tc); }
+
+__device__ __forceinline__ float imager_u(const GeomDev &G, int iu) { return fmaf((float)iu, G.du, G.u_first); }
+__device__ __forceinline__ float imager_v(const GeomDev &G, int iv) { return fmaf((float)iv, G.dv, G.v_first); }
+
+// Length of ray (d) per unit tau: |D - S|.
+__device__ __forceinline__ float ray_length(float dxr, float dyr, float v)
+{
+    return sqrtf(fmaf(dxr, dxr, fmaf(dyr, dyr, v * v)));
+}
+
+// Device-resident scalars of CGLS (Appendix 1), FP64.
+struct Scalars {
+    double gamma;    // ||s||^2
+    double delta;    // ||q||^2
+    double alpha;    // gamma / delta
+    double beta;     // gamma' / gamma
+    double rr;       // ||r||^2 (monitoring)
+    unsigned int flags; // bit 0: a reduction was not finite
+    unsigned int pad;
+};
+
+enum FinalizeOp { FIN_GAMMA = 0, FIN_ALPHA = 1, FIN_BETA = 2, FIN_RR = 3 };
+
+// Projector epilogues.
+enum ProjectMode {
+    PM_PLAIN = 0,      // out = |d| S                     (public P)
+    PM_Q_PRESCALED = 1,// out = |d| * q, q = |d| S; partial sums of q^2
+    PM_R_PRESCALED = 2,// out = |d| * (y - q); partial sums of (y - q)^2
+    PM_COUNT = 3       // count segments longer than a threshold
+};
+
+// ---- host side ----------------------------------------------------------------------
+
+// Optional per-launch timing (cbct_profiling_enable): events around each launch.
+struct ProfToken {
+    cudaEvent_t start;
+    int kind;
+};
+ProfToken prof_start(int kind, cudaStream_t st);
+void prof_stop(const ProfToken &t, cudaStream_t st);
+
+// Launch a kernel with optional timing and the launch counter:
+//   CBCT_TIMED(kind, stream, kernel<<<grid, block, smem, stream>>>(args...));
+#define CBCT_TIMED(kind, st, ...)                                                                  \
+    do {                                                                                           \
+        ::cbct::ProfToken _cbct_tok = ::cbct::prof_start((kind), (st));                            \
+        __VA_ARGS__;                                                                               \
+        ::cbct::prof_stop(_cbct_tok, (st));                                                        \
+        ::cbct::note_launch();                                                                     \
+    } while (0)
+
+cbct_status set_error(cbct_status st, const char *fmt, ...);
+cbct_status check_cuda(cudaError_t e, const char *what);
+void note_launch(unsigned n = 1);
+int device_sm_count();
+
+// Launchers (all asynchronous on `st`; return CBCT_ERR_CUDA on launch failure).
+// Volume element (ix, iy, iz) lives at ix*sx + iy*sy + iz*sz.
+int project_num_blocks(const GeomDev &G);
+cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long long sy,
+                           long long sz, const float *y, float *out, int mode,
+                           double *partials, float count_thr, cudaStream_t st);
+int backproject_num_blocks(const GeomDev &G);
+cbct_status launch_backproject(const GeomDev &G, const float *gt, float *out, long long sx,
+                               long long sy, long long sz, float *out2, double *partials,
+                               cudaStream_t st);
+cbct_status launch_prescale(const GeomDev &G, const float *g, float *gt, cudaStream_t st);
+
+cbct_status launch_tf_analyze(int n0, int n1, int n2, const float *f, float *alpha,
+                              cudaStream_t st);
+cbct_status launch_tf_synth_shrink(int n0, int n1, int n2, const float *alpha, float mu,
+                                   int positivity, float *f, cudaStream_t st);
+
+} // namespace cbct
+
+// Library-owned geometry handle.
+struct cbct_geometry {
+    cbct_geometry_desc desc; // angles points into `angles`
+    double *angles;          // host copy
+    int device;
+    float2 *d_cs;            // per-view (cos, sin)
+    float *d_scratch;        // public project/backproject scratch (lazily allocated)
+    size_t scratch_bytes;
+    void *d_ws;              // reconstruction workspace (lazily allocated)
+    size_t ws_bytes;
+};
+
+namespace cbct {
+GeomDev level_geom(const cbct_geometry *g, int level);
+cbct_status ensure_scratch(cbct_geometry *g, size_t bytes);
+}

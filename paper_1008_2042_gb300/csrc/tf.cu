@@ -1,0 +1,214 @@
+// Piecewise-linear tight frame (Section 2.1): analysis W, and vector shrinkage T_mu
+// (Eq. (2)) + synthesis W^T + positivity H.
+//
+// The 3-D filters are tensor products of h0 = [1,2,1]/4, h1 = sqrt(2)/4 [1,0,-1],
+// h2 = [-1,2,-1]/4, so both transforms run as three 3-tap passes. Arrays are addressed as
+// (i2 * n1 + i1) * n0 + i0 with i0 the contiguous axis; channel i = l + 3m + 9n applies
+// h_l along axis 0, h_m along axis 1 and h_n along axis 2. The boundary is periodic.
+//
+// GB300 mapping: a block owns a 32 x 8 tile of the (axis 0, axis 1) plane and marches
+// along axis 2, keeping the planes it needs in shared memory (with a one-voxel halo), so
+// every input value is read from DRAM once and every output written once; warps read
+// and write 128-byte rows along the contiguous axis. Both kernels are bandwidth bound:
+// 4 B in + 108 B out per voxel for W, 108 B in + 4 B out for the shrink/synthesis.
+#include "cbct_internal.cuh"
+
+namespace cbct {
+
+constexpr int TA = 32, TB = 8, TF_THREADS = TA * TB;
+constexpr float R2_4 = 0.35355339059327373f; // sqrt(2) / 4
+
+__device__ __forceinline__ int wrapi(int i, int n)
+{
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+// Analysis along one axis for the window (f(x-1), f(x), f(x+1)) = (p, c, n):
+// alpha_l(x) = h_l[-1] f(x+1) + h_l[0] f(x) + h_l[1] f(x-1).
+__device__ __forceinline__ void ana3(float p, float c, float n, float &o0, float &o1, float &o2)
+{
+    const float s = n + p;
+    o0 = fmaf(0.25f, s, 0.5f * c);
+    o1 = R2_4 * (n - p);
+    o2 = fmaf(-0.25f, s, 0.5f * c);
+}
+
+// Synthesis along one axis: sum_l sum_k h_l[k] a_l(x + k) from the three channels at
+// x-1 (P*), x (C*), x+1 (N*).
+__device__ __forceinline__ float syn3(float P0, float C0, float N0, float P1, float N1, float P2,
+                                      float C2, float N2)
+{
+    return fmaf(0.25f, (P0 + N0) - (P2 + N2), fmaf(0.5f, C0 + C2, R2_4 * (P1 - N1)));
+}
+
+static int tf_chunk(int n0, int n1, int n2)
+{
+    const long long tiles = (long long)((n0 + TA - 1) / TA) * ((n1 + TB - 1) / TB);
+    const long long want = 6LL * device_sm_count();
+    long long nch = (want + tiles - 1) / tiles;
+    if (nch < 1) nch = 1;
+    if (nch > n2) nch = n2;
+    return (int)((n2 + nch - 1) / nch);
+}
+
+__global__ void __launch_bounds__(TF_THREADS)
+k_tf_analyze(int n0, int n1, int n2, int chunk, const float *__restrict__ f, float *__restrict__ alpha)
+{
+    __shared__ float s[3][TB + 2][TA + 2];
+    const int a0 = blockIdx.x * TA, b0 = blockIdx.y * TB;
+    const int c_begin = blockIdx.z * chunk;
+    const int c_end = min(n2, c_begin + chunk);
+    if (c_begin >= c_end) return;
+    const int tid = threadIdx.y * TA + threadIdx.x;
+    const size_t N = (size_t)n0 * n1 * n2;
+
+    auto load_plane = [&](int c, int slot) {
+        const int cw = wrapi(c, n2);
+        for (int i = tid; i < (TA + 2) * (TB + 2); i += TF_THREADS) {
+            const int r = i / (TA + 2), q = i - r * (TA + 2);
+            const int ga = wrapi(a0 + q - 1, n0), gb = wrapi(b0 + r - 1, n1);
+            s[slot][r][q] = __ldg(f + ((size_t)cw * n1 + gb) * n0 + ga);
+        }
+    };
+    load_plane(c_begin - 1, 0);
+    load_plane(c_begin, 1);
+    const int ta = threadIdx.x, tb = threadIdx.y;
+    const bool inside = a0 + ta < n0 && b0 + tb < n1;
+    for (int c = c_begin; c < c_end; ++c) {
+        const int j = c - c_begin;
+        load_plane(c + 1, (j + 2) % 3);
+        __syncthreads();
+        if (inside) {
+            const int sl[3] = {j % 3, (j + 1) % 3, (j + 2) % 3}; // planes c-1, c, c+1
+            // axis 0 then axis 1: u[cc][m][l]
+            float u[3][3][3];
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                float t[3][3]; // [bb][l]
+#pragma unroll
+                for (int bb = 0; bb < 3; ++bb)
+                    ana3(s[sl[cc]][tb + bb][ta], s[sl[cc]][tb + bb][ta + 1], s[sl[cc]][tb + bb][ta + 2],
+                         t[bb][0], t[bb][1], t[bb][2]);
+#pragma unroll
+                for (int l = 0; l < 3; ++l) ana3(t[0][l], t[1][l], t[2][l], u[cc][0][l], u[cc][1][l], u[cc][2][l]);
+            }
+            const size_t o = ((size_t)c * n1 + (b0 + tb)) * n0 + (a0 + ta);
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    float w0, w1, w2;
+                    ana3(u[0][m][l], u[1][m][l], u[2][m][l], w0, w1, w2);
+                    __stcs(alpha + (size_t)(l + 3 * m) * N + o, w0);
+                    __stcs(alpha + (size_t)(l + 3 * m + 9) * N + o, w1);
+                    __stcs(alpha + (size_t)(l + 3 * m + 18) * N + o, w2);
+                }
+        }
+        __syncthreads();
+    }
+}
+
+constexpr int SA_PLANE = (TB + 2) * (TA + 2); // one channel of the haloed tile
+constexpr int SU_PLANE = (TB + 2) * TA;
+constexpr size_t TF_SYN_SMEM = sizeof(float) * (27 * SA_PLANE + 9 * SU_PLANE);
+
+__global__ void __launch_bounds__(TF_THREADS)
+k_tf_synth_shrink(int n0, int n1, int n2, int chunk, const float *__restrict__ alpha, float mu,
+                  int positivity, float *__restrict__ f)
+{
+    extern __shared__ float sm[];
+    float *sa = sm;                   // [27][TB+2][TA+2]: shrunk coefficients of one plane
+    float *su = sm + 27 * SA_PLANE;   // [9][TB+2][TA]: after synthesis along axis 0
+    const int a0 = blockIdx.x * TA, b0 = blockIdx.y * TB;
+    const int c_begin = blockIdx.z * chunk;
+    const int c_end = min(n2, c_begin + chunk);
+    if (c_begin >= c_end) return;
+    const int tid = threadIdx.y * TA + threadIdx.x;
+    const int ta = threadIdx.x, tb = threadIdx.y;
+    const size_t N = (size_t)n0 * n1 * n2;
+    const bool inside = a0 + ta < n0 && b0 + tb < n1;
+
+    float w_m2[3] = {0.f, 0.f, 0.f}, w_m1[3] = {0.f, 0.f, 0.f}; // w_n at planes c'-2, c'-1
+    for (int cp = c_begin - 1; cp <= c_end; ++cp) {
+        const int cw = wrapi(cp, n2);
+        // 1. coefficients of plane cp on the haloed tile
+        for (int i = tid; i < 27 * SA_PLANE; i += TF_THREADS) {
+            const int ch = i / SA_PLANE, rem = i - ch * SA_PLANE;
+            const int r = rem / (TA + 2), q = rem - r * (TA + 2);
+            const int ga = wrapi(a0 + q - 1, n0), gb = wrapi(b0 + r - 1, n1);
+            sa[i] = __ldg(alpha + (size_t)ch * N + ((size_t)cw * n1 + gb) * n0 + ga);
+        }
+        __syncthreads();
+        // 2. vector shrinkage, Eq. (2): scale the 26 high-pass channels of every position
+        for (int pos = tid; pos < SA_PLANE; pos += TF_THREADS) {
+            float s2 = 0.0f;
+#pragma unroll
+            for (int ch = 1; ch < 27; ++ch) {
+                const float a = sa[ch * SA_PLANE + pos];
+                s2 = fmaf(a, a, s2);
+            }
+            const float nrm = sqrtf(s2);
+            const float scale = nrm > mu ? 1.0f - mu / nrm : 0.0f;
+#pragma unroll
+            for (int ch = 1; ch < 27; ++ch) sa[ch * SA_PLANE + pos] *= scale;
+        }
+        __syncthreads();
+        // 3. synthesis along axis 0: u_{mn} = sum_l, for TA x (TB+2) positions
+        for (int i = tid; i < 9 * SU_PLANE; i += TF_THREADS) {
+            const int mn = i / SU_PLANE, rem = i - mn * SU_PLANE;
+            const int r = rem / TA, q = rem - r * TA;
+            const float *b0p = sa + (3 * mn) * SA_PLANE + r * (TA + 2) + q; // l = 0
+            const float *b1p = b0p + SA_PLANE, *b2p = b1p + SA_PLANE;
+            su[i] = syn3(b0p[0], b0p[1], b0p[2], b1p[0], b1p[2], b2p[0], b2p[1], b2p[2]);
+        }
+        __syncthreads();
+        // 4. synthesis along axis 1: w_n = sum_m
+        float w[3];
+#pragma unroll
+        for (int n = 0; n < 3; ++n) {
+            const float *m0 = su + (3 * n + 0) * SU_PLANE + tb * TA + ta;
+            const float *m1 = m0 + SU_PLANE, *m2 = m1 + SU_PLANE;
+            w[n] = syn3(m0[0], m0[TA], m0[2 * TA], m1[0], m1[2 * TA], m2[0], m2[TA], m2[2 * TA]);
+        }
+        // 5. synthesis along axis 2 gives plane cp - 1
+        if (cp >= c_begin + 1 && inside) {
+            float out = syn3(w_m2[0], w_m1[0], w[0], w_m2[1], w[1], w_m2[2], w_m1[2], w[2]);
+            if (positivity && out < 0.0f) out = 0.0f;
+            f[((size_t)(cp - 1) * n1 + (b0 + tb)) * n0 + (a0 + ta)] = out;
+        }
+#pragma unroll
+        for (int n = 0; n < 3; ++n) {
+            w_m2[n] = w_m1[n];
+            w_m1[n] = w[n];
+        }
+        __syncthreads();
+    }
+}
+
+cbct_status launch_tf_analyze(int n0, int n1, int n2, const float *f, float *alpha, cudaStream_t st)
+{
+    const int chunk = tf_chunk(n0, n1, n2);
+    dim3 grid((n0 + TA - 1) / TA, (n1 + TB - 1) / TB, (n2 + chunk - 1) / chunk);
+    CBCT_TIMED(CBCT_KERNEL_TF_ANALYZE, st, k_tf_analyze<<<grid, dim3(TA, TB), 0, st>>>(n0, n1, n2, chunk, f, alpha));
+    return check_cuda(cudaGetLastError(), "tf_analyze launch");
+}
+
+cbct_status launch_tf_synth_shrink(int n0, int n1, int n2, const float *alpha, float mu,
+                                   int positivity, float *f, cudaStream_t st)
+{
+    static bool attr_set = false; // per process; the attribute is per function
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_tf_synth_shrink, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)TF_SYN_SMEM);
+        if (e != cudaSuccess) return check_cuda(e, "tf_synth_shrink attribute");
+        attr_set = true;
+    }
+    const int chunk = tf_chunk(n0, n1, n2);
+    dim3 grid((n0 + TA - 1) / TA, (n1 + TB - 1) / TB, (n2 + chunk - 1) / chunk);
+    CBCT_TIMED(CBCT_KERNEL_TF_SYNTH, st,
+               k_tf_synth_shrink<<<grid, dim3(TA, TB), TF_SYN_SMEM, st>>>(n0, n1, n2, chunk, alpha, mu, positivity, f));
+    return check_cuda(cudaGetLastError(), "tf_synth_shrink launch");
+}
+
+} // namespace cbct

@@ -120,17 +120,24 @@ def voxel_centres(geom: Geometry):
 def voxelize(geom: Geometry, ellipsoids: Sequence[Ellipsoid]) -> np.ndarray:
     """Sample the phantom at voxel centres; later ellipsoids overwrite earlier ones.
 
-    Returns float64 (nz, ny, nx)."""
+    Returns float64 (nz, ny, nx). Each ellipsoid is evaluated only inside its bounding box."""
     x, y, z = voxel_centres(geom)
-    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
     f = np.zeros(geom.vol_shape, dtype=np.float64)
     for e in ellipsoids:
         c, s = math.cos(e.phi), math.sin(e.phi)
+        hx = math.hypot(e.ax * c, e.ay * s)
+        hy = math.hypot(e.ax * s, e.ay * c)
+        sel = [np.nonzero(np.abs(v - cen) <= h + 1e-9)[0]
+               for v, cen, h in ((z, e.cz, e.az), (y, e.cy, hy), (x, e.cx, hx))]
+        if any(len(q) == 0 for q in sel):
+            continue
+        (z0, z1), (y0, y1), (x0, x1) = [(q[0], q[-1] + 1) for q in sel]
+        Z, Y, X = np.meshgrid(z[z0:z1], y[y0:y1], x[x0:x1], indexing="ij")
         xr = (X - e.cx) * c + (Y - e.cy) * s
         yr = -(X - e.cx) * s + (Y - e.cy) * c
         zr = Z - e.cz
         inside = (xr / e.ax) ** 2 + (yr / e.ay) ** 2 + (zr / e.az) ** 2 <= 1.0
-        f[inside] = e.value
+        f[z0:z1, y0:y1, x0:x1][inside] = e.value
     return f
 
 

@@ -1,0 +1,164 @@
+"""Parity of the CUDA operators (through the C ABI) with the FP64 oracle, element by
+element on seeded inputs: P and P^T within relative L2 1e-4, W and the shrink/synthesis
+within 1e-5, the multigrid transfers within 1e-6."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cb():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1008_2042_gb300 import build
+    build.build()
+    import paper_1008_2042_gb300 as m
+    m.load_library()
+    return m
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float32, device="cuda")
+
+
+GEOMS = {
+    "small": synth.config_small(),
+    # odd sizes (ragged tiles in every kernel), anisotropic voxels, offsets, rotated start
+    "odd": synth.Geometry(nx=37, ny=29, nz=11, dx=1.7, dy=2.3, dz=1.1, nu=45, nv=23, du=1.9, dv=1.3,
+                          u_off=2.1, v_off=-1.7, n_views=7,
+                          angles=tuple(0.05 + 2 * np.pi * np.arange(7) / 7)),
+    # steep cone: many z crossings per ray, rays leaving through top and bottom
+    "cone": synth.Geometry(nx=24, ny=24, nz=12, dx=3.0, dy=3.0, dz=2.0, nu=40, nv=70, du=3.0, dv=6.0,
+                           n_views=5, angles=tuple(0.3 + 1.1 * np.arange(5))),
+    # one voxel
+    "one": synth.Geometry(nx=1, ny=1, nz=1, dx=10.0, dy=10.0, dz=10.0, nu=8, nv=6, du=2.0, dv=2.0,
+                          n_views=3, angles=(0.1, 1.0, 2.5)),
+    # nv larger than one block of rows; imager wider than 128
+    "tall": synth.Geometry(nx=40, ny=36, nz=20, dx=1.5, dy=1.5, dz=1.5, nu=150, nv=140, du=0.8, dv=0.7,
+                           n_views=4, angles=(0.2, 0.9, 2.2, 4.0)),
+}
+
+
+@pytest.mark.parametrize("name", list(GEOMS))
+def test_project_parity(cb, name):
+    geom = GEOMS[name]
+    f = synth.random_volume(geom, 101)
+    with cb.Geometry(geom) as g:
+        p = cb.project(g, dev(f)).cpu().numpy()
+    ref = oracle.project(geom, f)
+    assert rel(p, ref) <= 1e-4, rel(p, ref)
+
+
+@pytest.mark.parametrize("name", list(GEOMS))
+def test_backproject_parity(cb, name):
+    geom = GEOMS[name]
+    y = synth.random_projections(geom, 102)
+    with cb.Geometry(geom) as g:
+        b = cb.backproject(g, dev(y)).cpu().numpy()
+    ref = oracle.backproject(geom, y)
+    assert rel(b, ref) <= 1e-4, rel(b, ref)
+
+
+def test_project_phantom_parity(cb):
+    geom = synth.config_small()
+    f = synth.voxelize(geom, synth.random_ellipsoids(geom, 1001))
+    with cb.Geometry(geom) as g:
+        p = cb.project(g, dev(f)).cpu().numpy()
+    ref = oracle.project(geom, f)
+    assert rel(p, ref) <= 1e-5, rel(p, ref)
+
+
+@pytest.mark.parametrize("name", ["small", "odd", "cone"])
+def test_gpu_adjoint_identity(cb, name):
+    geom = GEOMS[name]
+    f = synth.random_volume(geom, 103)
+    y = synth.random_projections(geom, 104)
+    with cb.Geometry(geom) as g:
+        pf = cb.project(g, dev(f)).cpu().numpy().astype(np.float64)
+        bty = cb.backproject(g, dev(y)).cpu().numpy().astype(np.float64)
+    f32 = f.astype(np.float32).astype(np.float64)
+    y32 = y.astype(np.float32).astype(np.float64)
+    lhs, rhs = np.vdot(pf, y32), np.vdot(f32, bty)
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs), (lhs, rhs)
+
+
+def test_count_nnz_matches_oracle(cb):
+    for geom in (GEOMS["small"], GEOMS["odd"], GEOMS["cone"]):
+        with cb.Geometry(geom) as g:
+            n_gpu = cb.count_nnz(g)
+        n_ref = oracle.count_nnz(geom)
+        assert abs(n_gpu - n_ref) <= 5e-3 * n_ref, (n_gpu, n_ref)
+
+
+def test_count_nnz_levels(cb):
+    geom = synth.config_small()
+    with cb.Geometry(geom) as g:
+        for lev in (1, 2):
+            n_gpu = cb.count_nnz(g, lev)
+            n_ref = oracle.count_nnz(geom.level(lev))
+            assert abs(n_gpu - n_ref) <= 5e-3 * n_ref, (lev, n_gpu, n_ref)
+
+
+TF_SHAPES = [(16, 64, 64), (5, 6, 7), (1, 4, 3), (2, 3, 5), (9, 17, 33), (3, 70, 40)]
+
+
+@pytest.mark.parametrize("shape", TF_SHAPES)
+def test_tf_analyze_parity(cb, shape):
+    f = np.random.default_rng(5).standard_normal(shape)
+    a = cb.tf_analyze(dev(f)).cpu().numpy()
+    ref = oracle.tf_analyze(f)
+    assert rel(a, ref) <= 1e-5, rel(a, ref)
+    for i in (0, 1, 13, 26):  # every channel individually, including the low-pass
+        assert rel(a[i], ref[i]) <= 1e-5, (i, rel(a[i], ref[i]))
+
+
+@pytest.mark.parametrize("shape", TF_SHAPES)
+@pytest.mark.parametrize("positive", [False, True])
+def test_tf_synthesize_shrink_parity(cb, shape, positive):
+    rng = np.random.default_rng(6)
+    alpha = rng.standard_normal((27,) + shape) * 0.01
+    # threshold near the median high-pass norm: about half the voxels are zeroed
+    mu = float(np.median(np.sqrt((alpha[1:] ** 2).sum(0))))
+    out = cb.tf_synthesize_shrink(dev(alpha), mu, positive).cpu().numpy()
+    ref = oracle.tf_synthesize_shrink(alpha, mu, positive)
+    assert rel(out, ref) <= 1e-5, rel(out, ref)
+
+
+def test_tf_round_trip_identity(cb):
+    f = np.random.default_rng(7).standard_normal((16, 64, 64))
+    ft = dev(f)
+    back = cb.tf_synthesize_shrink(cb.tf_analyze(ft), 0.0, False).cpu().numpy()
+    assert rel(back, f) <= 1e-6
+
+
+def test_prolong_parity(cb):
+    fc = np.random.default_rng(8).uniform(0, 1, (9, 16, 12))
+    cs, fs, fshape = (2.0, 2.0, 5.0), (1.0, 1.0, 2.5), (18, 32, 24)
+    out = cb.prolong(dev(fc), cs, fshape, fs).cpu().numpy()
+    ref = oracle.prolong(fc, cs, fshape, fs)
+    assert rel(out, ref) <= 1e-6, rel(out, ref)
+    # odd fine sizes (non-nested grids), as on the paper's 70 -> 35 -> 18 slices
+    out = cb.prolong(dev(fc), cs, (17, 31, 23), fs).cpu().numpy()
+    ref = oracle.prolong(fc, cs, (17, 31, 23), fs)
+    assert rel(out, ref) <= 1e-6, rel(out, ref)
+
+
+def test_restrict_parity(cb):
+    ff = np.random.default_rng(9).uniform(0, 1, (17, 31, 24))
+    out = cb.restrict(dev(ff), (1.0, 1.0, 2.0), (9, 16, 12), (2.0, 2.0, 4.0)).cpu().numpy()
+    ref = oracle.restrict(ff, (1.0, 1.0, 2.0), (9, 16, 12), (2.0, 2.0, 4.0))
+    assert rel(out, ref) <= 1e-6, rel(out, ref)
