@@ -3,21 +3,23 @@
 //
 // GB300 mapping. All rays of one view that hit the same imager column u share their
 // transverse path through the (x, y) voxel columns; the imager row v only tilts them in
-// z. A block therefore owns one (view, column) pair and its threads own consecutive
-// rows: the 2-D Siddon walk over (x, y) columns is identical in every lane (warp-uniform
-// control flow, no divergence), and at each column a lane reads the voxel of its own
-// z slab. With the iteration's z-fastest volume layout the 32 lanes of a warp read a few
-// consecutive floats of one column — one or two 32-byte sectors per load. z-plane
-// crossings (about one per 40 column steps at the paper's sizes) are handled by a short
-// per-lane loop. Accumulation is FP32; the epilogue can scale by |D - S|, form the
-// CGLS residual and reduce squared norms in FP64 into one partial per block.
+// z. A block owns one (view, column) pair and its threads own the imager rows. The
+// block first computes the shared transverse Siddon trace once, cooperatively, into
+// shared memory (a parallel merge of the x-plane and y-plane crossing lists). Each lane
+// then walks that list, reading the voxel of its own z slab in every column; with the
+// iteration's z-fastest volume layout the 32 lanes of a warp read a few consecutive
+// floats of one column, one or two 32-byte sectors per load. Columns are processed in
+// unrolled groups whose loads are all in flight together; the rare columns in which a
+// lane crosses a z plane are corrected afterwards. Accumulation is FP32; the epilogue can
+// scale by |D - S|, form the CGLS residual and reduce squared norms in FP64 into one
+// partial per block.
 #include <cfloat>
 
 #include "cbct_internal.cuh"
 
 namespace cbct {
 
-constexpr int PROJ_ROWS = 128;
+constexpr int PROJ_ROWS = 512; // at most this many imager rows per block
 constexpr float P_INF = 3.0e38f;
 
 static inline int proj_rows(const GeomDev &G)
@@ -32,34 +34,72 @@ int project_num_blocks(const GeomDev &G)
     return G.nviews * G.nu * ((G.nv + rows - 1) / rows);
 }
 
-__device__ __forceinline__ double block_sum(double v, double *s_warp)
+// Number of column segments a lane processes per unrolled group.
+constexpr int SEG_GROUP = 8;
+
+__device__ __forceinline__ int lower_count(const float *a, int n, float t) // # a[i] < t
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_warp[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-        for (int w = 0; w < nw; ++w) t += s_warp[w];
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < t) lo = mid + 1;
+        else hi = mid;
     }
-    return t;
+    return lo;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(PROJ_ROWS)
-k_project(GeomDev G, const float *__restrict__ f, long long sx, long long sy, long long sz,
-          const float *__restrict__ y, float *__restrict__ out, double *__restrict__ partials,
-          float count_thr)
+__device__ __forceinline__ int upper_count(const float *a, int n, float t) // # a[i] <= t
 {
-    __shared__ double s_warp[PROJ_ROWS / 32];
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] <= t) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+static inline int seg_capacity(const GeomDev &G)
+{
+    return ((G.nx + G.ny + 3 + SEG_GROUP - 1) / SEG_GROUP + 1) * SEG_GROUP;
+}
+
+// sA, sB (crossing lists), then sEnd and sCol aligned to 16 bytes for vector loads
+static inline int seg_offset(const GeomDev &G) { return ((G.nx + G.ny + 2 + 3) / 4) * 4; }
+
+static inline size_t project_smem(const GeomDev &G)
+{
+    return sizeof(float) * (size_t)seg_offset(G) + (sizeof(float) + sizeof(int)) * (size_t)seg_capacity(G);
+}
+
+// One block per (view, imager column, chunk of rows). Phase 1 (whole block): the
+// transverse Siddon trace of the column's rays — the crossings with the x planes and
+// with the y planes are each increasing in tau, so every crossing's position in the
+// merged order is its own index plus the number of crossings of the other family before
+// it (binary search); this yields the list of (x, y) voxel columns the rays visit and
+// the tau at which each is left. Phase 2 (one lane per imager row): walk that list in
+// groups of SEG_GROUP columns, load all of the group's voxels at the lane's current z
+// slab at once, and correct the few columns in which the lane crosses a z plane.
+template <int MODE>
+__global__ void __launch_bounds__(512)
+k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, int sz, const float *__restrict__ y,
+          float *__restrict__ out, double *__restrict__ partials, float count_thr)
+{
+    extern __shared__ float smem[];
+    __shared__ double s_warp[16];
+    float *sA = smem;                      // x-plane crossings, in ray order
+    float *sB = sA + (G.nx + 1);           // y-plane crossings
+    const int cap = ((G.nx + G.ny + 3 + SEG_GROUP - 1) / SEG_GROUP + 1) * SEG_GROUP;
+    float *sEnd = smem + ((G.nx + G.ny + 2 + 3) / 4) * 4; // tau at which segment j ends (16-B aligned)
+    int *sCol = reinterpret_cast<int *>(sEnd + cap); // voxel-column offset of segment j
+
+    const int tid = threadIdx.x, nthr = blockDim.x;
     const int view = blockIdx.x / G.nu;
     const int iu = blockIdx.x - view * G.nu;
-    const int iv = blockIdx.y * blockDim.x + threadIdx.x;
+    const int iv = blockIdx.y * blockDim.x + tid;
     const bool row_ok = iv < G.nv;
 
-    // ---- transverse ray (uniform over the block) ----
+    // ---- transverse ray, shared by every row ----
     const float2 cs = G.cs[view];
     float dxr, dyr, qx, qy;
     ray_xy(G, cs.x, cs.y, imager_u(G, iu), dxr, dyr, qx, qy);
@@ -68,80 +108,140 @@ k_project(GeomDev G, const float *__restrict__ f, long long sx, long long sy, lo
     const float ya = tau_plane(G.y0, qy, inv_y), yb = tau_plane(plane_at(G.ny, G.dy, G.y0), qy, inv_y);
     const float tau_in = fmaxf(fmaxf(fminf(xa, xb), fminf(ya, yb)), -G.tc);
     const float tau_out = fminf(fminf(fmaxf(xa, xb), fmaxf(ya, yb)), 1.0f - G.tc);
-
+    const bool hit = tau_in < tau_out;
     const int sxs = dxr > 0.0f ? 1 : -1, sys = dyr > 0.0f ? 1 : -1;
-    int ix = (int)floorf((fmaf(tau_in, dxr, qx) - G.x0) / G.dx);
-    int iy = (int)floorf((fmaf(tau_in, dyr, qy) - G.y0) / G.dy);
-    ix = min(max(ix, 0), G.nx - 1);
-    iy = min(max(iy, 0), G.ny - 1);
-    float txn = dxr != 0.0f ? tau_plane(plane_at(ix + (sxs > 0), G.dx, G.x0), qx, inv_x) : P_INF;
-    float tyn = dyr != 0.0f ? tau_plane(plane_at(iy + (sys > 0), G.dy, G.y0), qy, inv_y) : P_INF;
-    // a crossing computed at or before the entry point has already been passed
-    for (int r = 0; r < 2 && txn <= tau_in; ++r) {
-        ix += sxs;
-        txn = tau_plane(plane_at(ix + (sxs > 0), G.dx, G.x0), qx, inv_x);
-    }
-    for (int r = 0; r < 2 && tyn <= tau_in; ++r) {
-        iy += sys;
-        tyn = tau_plane(plane_at(iy + (sys > 0), G.dy, G.y0), qy, inv_y);
-    }
-    const bool hit = tau_in < tau_out && (unsigned)ix < (unsigned)G.nx && (unsigned)iy < (unsigned)G.ny;
 
-    // ---- per-lane z state ----
+    // ---- phase 1: crossings of each plane family, then their merged order ----
+    int a_le = 0, a_in = 0, b_le = 0, b_in = 0;
+    for (int a0 = 0; a0 <= G.nx; a0 += nthr) {
+        const int a = a0 + tid;
+        bool le = false, in = false;
+        if (a <= G.nx && hit && dxr != 0.0f) {
+            const float t = tau_plane(plane_at(dxr > 0.0f ? a : G.nx - a, G.dx, G.x0), qx, inv_x);
+            sA[a] = t;
+            le = t <= tau_in;
+            in = t > tau_in && t < tau_out;
+        }
+        a_le += __syncthreads_count(le);
+        a_in += __syncthreads_count(in);
+    }
+    for (int b0 = 0; b0 <= G.ny; b0 += nthr) {
+        const int b = b0 + tid;
+        bool le = false, in = false;
+        if (b <= G.ny && hit && dyr != 0.0f) {
+            const float t = tau_plane(plane_at(dyr > 0.0f ? b : G.ny - b, G.dy, G.y0), qy, inv_y);
+            sB[b] = t;
+            le = t <= tau_in;
+            in = t > tau_in && t < tau_out;
+        }
+        b_le += __syncthreads_count(le);
+        b_in += __syncthreads_count(in);
+    }
+    const float *LA = sA + a_le, *LB = sB + b_le;
+    const int nA = a_in, nB = b_in, nseg = nA + nB + 1;
+    // the column entered first contains the midpoint of the first segment
+    float e0 = tau_out;
+    if (nA) e0 = fminf(e0, LA[0]);
+    if (nB) e0 = fminf(e0, LB[0]);
+    const float tm = 0.5f * (tau_in + e0);
+    const int ix_e = min(max((int)floorf((fmaf(tm, dxr, qx) - G.x0) / G.dx), 0), G.nx - 1);
+    const int iy_e = min(max((int)floorf((fmaf(tm, dyr, qy) - G.y0) / G.dy), 0), G.ny - 1);
+    for (int i = tid; i < nA; i += nthr) {
+        const float t = LA[i];
+        const int nb = lower_count(LB, nB, t), r = i + nb;
+        const int cx = min(max(ix_e + sxs * (i + 1), 0), G.nx - 1), cy = min(max(iy_e + sys * nb, 0), G.ny - 1);
+        sEnd[r] = t;
+        sCol[r + 1] = cx * sx + cy * sy;
+    }
+    for (int j = tid; j < nB; j += nthr) {
+        const float t = LB[j];
+        const int na = upper_count(LA, nA, t), r = j + na;
+        const int cx = min(max(ix_e + sxs * na, 0), G.nx - 1), cy = min(max(iy_e + sys * (j + 1), 0), G.ny - 1);
+        sEnd[r] = t;
+        sCol[r + 1] = cx * sx + cy * sy;
+    }
+    const int col0 = ix_e * sx + iy_e * sy;
+    if (tid == 0) {
+        sCol[0] = col0;
+        sEnd[nseg - 1] = tau_out;
+    }
+    for (int q = nseg + tid; q < cap; q += nthr) { // zero-length padding up to whole groups
+        sEnd[q] = tau_out;
+        sCol[q] = col0;
+    }
+    __syncthreads();
+
+    // ---- phase 2: per-lane z state ----
     const float v = imager_v(G, iv);
     const float inv_v = v != 0.0f ? __frcp_rn(v) : 1e30f;
     const int skz = v >= 0.0f ? 1 : -1;
     int kz = (int)floorf((v * (G.tc + tau_in) - G.z0) / G.dz);
     bool active = hit && row_ok && kz >= 0 && kz < G.nz;
     float tzn = active ? tau_zplane(plane_at(kz + (skz > 0), G.dz, G.z0), inv_v, G.tc) : P_INF;
-    if (active && tzn <= tau_in) {
+    if (active && tzn <= tau_in) { // the entry point already lies past that plane
         kz += skz;
-        if ((unsigned)kz >= (unsigned)G.nz) {
-            active = false;
-            tzn = P_INF;
-        } else {
-            tzn = tau_zplane(plane_at(kz + (skz > 0), G.dz, G.z0), inv_v, G.tc);
-        }
+        active = (unsigned)kz < (unsigned)G.nz;
+        tzn = active ? tau_zplane(plane_at(kz + (skz > 0), G.dz, G.z0), inv_v, G.tc) : P_INF;
     }
     const float L = ray_length(dxr, dyr, v);
-    const float thr_tau = MODE == PM_COUNT ? count_thr / L : 0.0f;
 
     float acc = 0.0f;
     int cnt = 0;
-    if (hit) {
-        float tau = tau_in;
-        const int max_steps = G.nx + G.ny + 2;
-        for (int step = 0; step < max_steps; ++step) {
-            const float tnext = fminf(fminf(txn, tyn), tau_out);
-            const long long col = (long long)ix * sx + (long long)iy * sy;
-            float tl = tau;
-            while (tzn < tnext) { // z-plane crossing inside this column (lane-divergent, rare)
-                if (MODE == PM_COUNT) cnt += (tzn - tl) > thr_tau;
-                else acc = fmaf(__ldg(f + col + kz * sz), tzn - tl, acc);
-                tl = tzn;
+    if (hit && MODE == PM_COUNT) {
+        const float thr_tau = count_thr / L;
+        float s0 = tau_in;
+        for (int j = 0; j < nseg; ++j) {
+            const float e = sEnd[j];
+            float sl = s0;
+            while (tzn < e) {
+                cnt += (tzn - sl) > thr_tau;
+                sl = tzn;
                 kz += skz;
-                if ((unsigned)kz >= (unsigned)G.nz) {
-                    active = false;
-                    tzn = P_INF;
-                } else {
-                    tzn = tau_zplane(plane_at(kz + (skz > 0), G.dz, G.z0), inv_v, G.tc);
+                active = (unsigned)kz < (unsigned)G.nz;
+                tzn = active ? tau_zplane(plane_at(kz + (skz > 0), G.dz, G.z0), inv_v, G.tc) : P_INF;
+            }
+            if (active) cnt += (e - sl) > thr_tau;
+            s0 = e;
+        }
+    } else if (hit) {
+        float sprev = tau_in;
+        for (int j = 0; j < nseg; j += SEG_GROUP) {
+            float e[SEG_GROUP], st[SEG_GROUP], val[SEG_GROUP];
+            int c[SEG_GROUP];
+#pragma unroll
+            for (int u = 0; u < SEG_GROUP; u += 4) {
+                const float4 e4 = *reinterpret_cast<const float4 *>(sEnd + j + u);
+                const int4 c4 = *reinterpret_cast<const int4 *>(sCol + j + u);
+                e[u] = e4.x; e[u + 1] = e4.y; e[u + 2] = e4.z; e[u + 3] = e4.w;
+                c[u] = c4.x; c[u + 1] = c4.y; c[u + 2] = c4.z; c[u + 3] = c4.w;
+            }
+            st[0] = sprev;
+#pragma unroll
+            for (int u = 1; u < SEG_GROUP; ++u) st[u] = e[u - 1];
+            const int koff = kz * sz;
+#pragma unroll
+            for (int u = 0; u < SEG_GROUP; ++u) val[u] = active ? __ldg(f + koff + c[u]) : 0.0f;
+#pragma unroll
+            for (int u = 0; u < SEG_GROUP; ++u) acc = fmaf(val[u], e[u] - st[u], acc);
+            const float gend = e[SEG_GROUP - 1];
+            while (tzn < gend) { // the lane crosses z planes inside this group (lane-divergent)
+                const int knew = kz + skz;
+                const bool anew = (unsigned)knew < (unsigned)G.nz;
+                const int noff = knew * sz;
+#pragma unroll
+                for (int u = 0; u < SEG_GROUP; ++u) {
+                    const float part = e[u] - fmaxf(st[u], tzn); // piece of column u past the plane
+                    if (part > 0.0f) {
+                        const float vn = anew ? __ldg(f + noff + c[u]) : 0.0f;
+                        acc = fmaf(vn - val[u], part, acc);
+                        val[u] = vn;
+                    }
                 }
+                kz = knew;
+                active = anew;
+                tzn = anew ? tau_zplane(plane_at(kz + (skz > 0), G.dz, G.z0), inv_v, G.tc) : P_INF;
             }
-            if (active) {
-                if (MODE == PM_COUNT) cnt += (tnext - tl) > thr_tau;
-                else acc = fmaf(__ldg(f + col + kz * sz), tnext - tl, acc);
-            }
-            if (tnext >= tau_out) break;
-            tau = tnext;
-            if (txn <= tyn) {
-                ix += sxs;
-                if ((unsigned)ix >= (unsigned)G.nx) break;
-                txn = tau_plane(plane_at(ix + (sxs > 0), G.dx, G.x0), qx, inv_x);
-            } else {
-                iy += sys;
-                if ((unsigned)iy >= (unsigned)G.ny) break;
-                tyn = tau_plane(plane_at(iy + (sys > 0), G.dy, G.y0), qy, inv_y);
-            }
+            sprev = gend;
         }
     }
 
@@ -164,8 +264,15 @@ k_project(GeomDev G, const float *__restrict__ f, long long sx, long long sy, lo
         }
     }
     if (MODE != PM_PLAIN) {
-        const double t = block_sum(red, s_warp);
-        if (threadIdx.x == 0) partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) red += __shfl_down_sync(0xffffffffu, red, o);
+        if ((tid & 31) == 0) s_warp[tid >> 5] = red;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (nthr + 31) / 32; ++w) t += s_warp[w];
+            partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+        }
     }
 }
 
@@ -175,19 +282,31 @@ cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long 
 {
     const int rows = proj_rows(G);
     dim3 grid((unsigned)(G.nviews * G.nu), (unsigned)((G.nv + rows - 1) / rows));
+    const size_t smem = project_smem(G);
+    static bool attr_set[4] = {false, false, false, false};
+    if (!attr_set[mode & 3]) {
+        const void *fn = mode == PM_PLAIN ? (const void *)k_project<PM_PLAIN>
+                       : mode == PM_Q_PRESCALED ? (const void *)k_project<PM_Q_PRESCALED>
+                       : mode == PM_R_PRESCALED ? (const void *)k_project<PM_R_PRESCALED>
+                                                : (const void *)k_project<PM_COUNT>;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        if (e != cudaSuccess) return check_cuda(e, "project attribute");
+        attr_set[mode & 3] = true;
+    }
+    const int isx = (int)sx, isy = (int)sy, isz = (int)sz;
     ProfToken tok = prof_start(CBCT_KERNEL_PROJECT, st);
     switch (mode) {
     case PM_PLAIN:
-        k_project<PM_PLAIN><<<grid, rows, 0, st>>>(G, f, sx, sy, sz, y, out, partials, count_thr);
+        k_project<PM_PLAIN><<<grid, rows, smem, st>>>(G, f, isx, isy, isz, y, out, partials, count_thr);
         break;
     case PM_Q_PRESCALED:
-        k_project<PM_Q_PRESCALED><<<grid, rows, 0, st>>>(G, f, sx, sy, sz, y, out, partials, count_thr);
+        k_project<PM_Q_PRESCALED><<<grid, rows, smem, st>>>(G, f, isx, isy, isz, y, out, partials, count_thr);
         break;
     case PM_R_PRESCALED:
-        k_project<PM_R_PRESCALED><<<grid, rows, 0, st>>>(G, f, sx, sy, sz, y, out, partials, count_thr);
+        k_project<PM_R_PRESCALED><<<grid, rows, smem, st>>>(G, f, isx, isy, isz, y, out, partials, count_thr);
         break;
     default:
-        k_project<PM_COUNT><<<grid, rows, 0, st>>>(G, f, sx, sy, sz, y, out, partials, count_thr);
+        k_project<PM_COUNT><<<grid, rows, smem, st>>>(G, f, isx, isy, isz, y, out, partials, count_thr);
         break;
     }
     prof_stop(tok, st);

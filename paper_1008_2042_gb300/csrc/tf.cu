@@ -63,13 +63,23 @@ k_tf_analyze(int n0, int n1, int n2, int chunk, const float *__restrict__ f, flo
     const int tid = threadIdx.y * TA + threadIdx.x;
     const size_t N = (size_t)n0 * n1 * n2;
 
-    auto load_plane = [&](int c, int slot) {
-        const int cw = wrapi(c, n2);
-        for (int i = tid; i < (TA + 2) * (TB + 2); i += TF_THREADS) {
-            const int r = i / (TA + 2), q = i - r * (TA + 2);
-            const int ga = wrapi(a0 + q - 1, n0), gb = wrapi(b0 + r - 1, n1);
-            s[slot][r][q] = __ldg(f + ((size_t)cw * n1 + gb) * n0 + ga);
+    int off[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int pos = tid + k * TF_THREADS;
+        if (pos < (TA + 2) * (TB + 2)) {
+            const int r = pos / (TA + 2), q = pos - r * (TA + 2);
+            off[k] = wrapi(b0 + r - 1, n1) * n0 + wrapi(a0 + q - 1, n0);
+        } else {
+            off[k] = -1;
         }
+    }
+    auto load_plane = [&](int c, int slot) {
+        const float *src = f + (size_t)wrapi(c, n2) * n1 * n0;
+        float *d = &s[slot][0][0];
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            if (off[k] >= 0) d[tid + k * TF_THREADS] = __ldg(src + off[k]);
     };
     load_plane(c_begin - 1, 0);
     load_plane(c_begin, 1);
@@ -129,15 +139,33 @@ k_tf_synth_shrink(int n0, int n1, int n2, int chunk, const float *__restrict__ a
     const size_t N = (size_t)n0 * n1 * n2;
     const bool inside = a0 + ta < n0 && b0 + tb < n1;
 
+    // in-plane source offset of the (at most two) haloed-tile positions this thread loads
+    int off[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int pos = tid + k * TF_THREADS;
+        if (pos < SA_PLANE) {
+            const int r = pos / (TA + 2), q = pos - r * (TA + 2);
+            off[k] = wrapi(b0 + r - 1, n1) * n0 + wrapi(a0 + q - 1, n0);
+        } else {
+            off[k] = -1;
+        }
+    }
     float w_m2[3] = {0.f, 0.f, 0.f}, w_m1[3] = {0.f, 0.f, 0.f}; // w_n at planes c'-2, c'-1
     for (int cp = c_begin - 1; cp <= c_end; ++cp) {
         const int cw = wrapi(cp, n2);
-        // 1. coefficients of plane cp on the haloed tile
-        for (int i = tid; i < 27 * SA_PLANE; i += TF_THREADS) {
-            const int ch = i / SA_PLANE, rem = i - ch * SA_PLANE;
-            const int r = rem / (TA + 2), q = rem - r * (TA + 2);
-            const int ga = wrapi(a0 + q - 1, n0), gb = wrapi(b0 + r - 1, n1);
-            sa[i] = __ldg(alpha + (size_t)ch * N + ((size_t)cw * n1 + gb) * n0 + ga);
+        // 1. coefficients of plane cp on the haloed tile (the in-plane offsets are fixed)
+        {
+            const float *src = alpha + (size_t)cw * n1 * n0;
+#pragma unroll 1
+            for (int k = 0; k < 2; ++k) {
+                if (off[k] >= 0) {
+                    const float *p = src + off[k];
+                    float *d = sa + tid + k * TF_THREADS;
+#pragma unroll 9
+                    for (int ch = 0; ch < 27; ++ch) d[ch * SA_PLANE] = __ldg(p + (size_t)ch * N);
+                }
+            }
         }
         __syncthreads();
         // 2. vector shrinkage, Eq. (2): scale the 26 high-pass channels of every position

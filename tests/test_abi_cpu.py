@@ -52,7 +52,7 @@ def _desc(**kw):
 
 
 @pytest.mark.parametrize("bad", [dict(nx=0), dict(dz=-1.0), dict(sdd=900.0), dict(n_views=0),
-                                 dict(nv=9000), dict(nx=4000, dx=1.0), dict(du=float("nan"))])
+                                 dict(nv=9000), dict(nx=4000, dx=1.0), dict(nx=4000, ny=4500, dx=0.01, dy=0.01), dict(du=float("nan"))])
 def test_invalid_geometry_is_rejected_before_device_work(lib, bad):
     d = _desc(**bad)
     h = ctypes.c_void_p()
