@@ -101,7 +101,8 @@ cbct_status cbct_project(const cbct_geometry *geom, const float *f, float *g,
  * result does not depend on scheduling). The paper's own backprojector (Eq. (3)) is an
  * approximation of this operator and is not what this call computes.
  * g: device [n_views][nv][nu]; f: device [nz][ny][nx]. FP32 arithmetic.
- * Uses the geometry's scratch (allocated on first use: one projection stack).
+ * Uses the geometry's scratch (allocated on first use: per-column row prefix sums,
+ * n_views * nu * (nv + 1) float pairs).
  */
 cbct_status cbct_backproject(const cbct_geometry *geom, const float *g, float *f,
                              cbct_stream_t stream);

@@ -2,19 +2,20 @@
 //
 // The paper replaces the adjoint by the closed form of Eq. (3) because a ray-driven
 // scatter would make threads collide on voxels (Section 2.2.2). Here the exact transpose
-// is computed as a gather instead: each thread owns one (x, y) voxel column and a chunk
-// of ZC consecutive z voxels, and for every view enumerates exactly the rays that can
-// cross it. The geometry separates: ray (u, v) meets column (ix, iy) over a tau interval
-// [ta, tb] that depends on u only, and meets z slab k over an interval that depends on v
-// only, so
+// is computed as a gather: each thread owns one (x, y) voxel column and a chunk of ZC
+// consecutive z voxels and, for every view, visits exactly the rays that can cross it.
+// The geometry separates: ray (u, v) meets column (ix, iy) over a tau interval [ta, tb]
+// that depends on u only, and meets z slab k over an interval that depends on v only, so
 //   a_ij = |D - S| * max(0, min(tb, tz1(v)) - max(ta, tz0(v))).
-// The candidate columns u come from the shadow of the column's four corners, the
-// candidate rows of each (u, slab) pair from the slab's z range seen over [ta, tb]. The
-// factor |D - S| is folded into the input beforehand (k_prescale, or the projector's
-// prescaled epilogue inside CGLS). Every crossing parameter is computed with the same
-// helper expressions as the projector, so both operators use the same FP32 weights.
-// No atomics: the result is independent of scheduling. Lanes of a warp are adjacent x
-// voxels, which see adjacent imager columns of the same rows: loads coalesce.
+// Candidate imager columns u come from the shadow of the voxel column's corners. For one
+// u, almost every row whose ray reaches slab k stays inside it across the whole column
+// and so has weight (tb - ta): those rows form a contiguous range and are summed at once
+// from per-column prefix sums over rows (k_row_prefix); only the rows whose ray crosses
+// a z plane inside the column (about 0.1 per plane at the paper's sizes) are evaluated
+// one by one. The factor |D - S| is folded into the prefix sums. Every crossing parameter
+// uses the same helper expressions as the projector, so both operators use the same
+// FP32 weights. No atomics: the result is independent of scheduling. Lanes of a warp are
+// adjacent x voxels, which read adjacent imager columns.
 #include "cbct_internal.cuh"
 
 namespace cbct {
@@ -36,10 +37,23 @@ int backproject_num_blocks(const GeomDev &G)
     return ((G.nx + BP_TX - 1) / BP_TX) * ((G.ny + BP_TY - 1) / BP_TY) * ((G.nz + zc - 1) / zc);
 }
 
+// Rows whose ray, while inside the column (tau in [ta, tb], 1/(tc+ta) = A, 1/(tc+tb) = B),
+// reaches the plane z = zp: v (tc + tau) = zp for some tau, i.e. v between zp*A and zp*B.
+// Returned as a widened integer row range (may extend outside [0, nv-1]).
+__device__ __forceinline__ void straddle_rows(const GeomDev &G, float zp, float A, float B, int &lo, int &hi)
+{
+    const float v0 = zp * A, v1 = zp * B;
+    const float lim = (float)(G.nv + 1);
+    const float flo = fminf(fmaxf(fmaf(fminf(v0, v1) - G.v_first, G.inv_dv, -1e-3f), -2.0f), lim);
+    const float fhi = fminf(fmaxf(fmaf(fmaxf(v0, v1) - G.v_first, G.inv_dv, 1e-3f), -2.0f), lim);
+    lo = (int)ceilf(flo);
+    hi = (int)floorf(fhi);
+}
+
 template <int ZC>
 __global__ void __launch_bounds__(BP_TX *BP_TY)
-k_backproject(GeomDev G, const float *__restrict__ gt, float *__restrict__ out, long long sx,
-              long long sy, long long sz, float *__restrict__ out2, double *__restrict__ partials)
+k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out, int sx, int sy, int sz,
+              float *__restrict__ out2, double *__restrict__ partials)
 {
     extern __shared__ float s_invv[]; // 1 / v per imager row
     __shared__ double s_warp[BP_TX * BP_TY / 32];
@@ -65,6 +79,7 @@ k_backproject(GeomDev G, const float *__restrict__ gt, float *__restrict__ out, 
 #pragma unroll
         for (int z = 0; z <= ZC; ++z) zp[z] = plane_at(iz0 + z, G.dz, G.z0);
         const int nzc = min(ZC, G.nz - iz0); // valid voxels in this chunk
+        const size_t col_stride = (size_t)G.nv + 1;
 
         for (int k = 0; k < G.nviews; ++k) {
             const float2 cs = G.cs[k];
@@ -81,7 +96,6 @@ k_backproject(GeomDev G, const float *__restrict__ gt, float *__restrict__ out, 
             }
             const int iu_lo = max(0, (int)ceilf(fmaf(umin - G.u_first, G.inv_du, -1e-3f)));
             const int iu_hi = min(G.nu - 1, (int)floorf(fmaf(umax - G.u_first, G.inv_du, 1e-3f)));
-            const float *gk = gt + (size_t)k * G.nv * G.nu;
 
             for (int iu = iu_lo; iu <= iu_hi; ++iu) {
                 float dxr, dyr, qx, qy;
@@ -92,25 +106,42 @@ k_backproject(GeomDev G, const float *__restrict__ gt, float *__restrict__ out, 
                 const float ta = fmaxf(fminf(t0, t1), fminf(t2, t3));
                 const float tb = fminf(fmaxf(t0, t1), fmaxf(t2, t3));
                 if (!(tb > ta)) continue;
-                // rows whose ray reaches slab [zl, zh] while inside the column:
-                // v (tc + tau) in [zl, zh] for some tau in [ta, tb]
                 const float A = __frcp_rn(G.tc + ta), B = __frcp_rn(G.tc + tb);
-                const float *gcol = gk + iu;
+                const float wfull = tb - ta;
+                const float2 *col = ps + ((size_t)k * G.nu + iu) * col_stride;
+                int lo_p, hi_p;
+                straddle_rows(G, zp[0], A, B, lo_p, hi_p);
 #pragma unroll
                 for (int z = 0; z < ZC; ++z) {
                     if (z >= nzc) break;
-                    const float zl = zp[z], zh = zp[z + 1];
-                    const float vlo = fminf(zl * A, zl * B), vhi = fmaxf(zh * A, zh * B);
-                    const int iv_lo = max(0, (int)ceilf(fmaf(vlo - G.v_first, G.inv_dv, -1e-3f)));
-                    const int iv_hi = min(G.nv - 1, (int)floorf(fmaf(vhi - G.v_first, G.inv_dv, 1e-3f)));
+                    int lo_n, hi_n;
+                    straddle_rows(G, zp[z + 1], A, B, lo_n, hi_n);
                     float a = acc[z];
-                    for (int iv = iv_lo; iv <= iv_hi; ++iv) {
+                    // rows strictly between the two planes' straddle ranges stay in the slab over
+                    // the whole column: each contributes g * (tb - ta); sum them from the prefix
+                    const int f0 = max(hi_p + 1, 0), f1 = min(lo_n - 1, G.nv - 1);
+                    if (f0 <= f1) {
+                        const float2 P1 = __ldg(col + f1 + 1), P0 = __ldg(col + f0);
+                        a = fmaf(wfull, (P1.x - P0.x) + (P1.y - P0.y), a);
+                    }
+                    // rows that cross a z plane inside the column: exact overlap
+                    const int r0 = max(lo_p, 0), r1 = min(hi_n, G.nv - 1);
+                    for (int iv = r0; iv <= r1; ++iv) {
+                        if (iv == f0 && f0 <= f1) { // already counted
+                            iv = f1;
+                            continue;
+                        }
                         const float iw = s_invv[iv];
-                        const float s0 = tau_zplane(zl, iw, G.tc), s1 = tau_zplane(zh, iw, G.tc);
+                        const float s0 = tau_zplane(zp[z], iw, G.tc), s1 = tau_zplane(zp[z + 1], iw, G.tc);
                         const float lo = fmaxf(ta, fminf(s0, s1)), hi = fminf(tb, fmaxf(s0, s1));
-                        if (hi > lo) a = fmaf(__ldg(gcol + (size_t)iv * G.nu), hi - lo, a);
+                        if (hi > lo) {
+                            const float2 Q1 = __ldg(col + iv + 1), Q0 = __ldg(col + iv);
+                            a = fmaf((Q1.x - Q0.x) + (Q1.y - Q0.y), hi - lo, a);
+                        }
                     }
                     acc[z] = a;
+                    lo_p = lo_n;
+                    hi_p = hi_n;
                 }
             }
         }
@@ -142,49 +173,61 @@ k_backproject(GeomDev G, const float *__restrict__ gt, float *__restrict__ out, 
     }
 }
 
-cbct_status launch_backproject(const GeomDev &G, const float *gt, float *out, long long sx,
-                               long long sy, long long sz, float *out2, double *partials,
-                               cudaStream_t st)
+cbct_status launch_backproject(const GeomDev &G, const float2 *ps, float *out, long long sx, long long sy,
+                               long long sz, float *out2, double *partials, cudaStream_t st)
 {
     const int zc = bp_zchunk(G);
     dim3 block(BP_TX, BP_TY);
     dim3 grid((G.nx + BP_TX - 1) / BP_TX, (G.ny + BP_TY - 1) / BP_TY, (G.nz + zc - 1) / zc);
     const size_t smem = sizeof(float) * G.nv;
+    const int isx = (int)sx, isy = (int)sy, isz = (int)sz;
     ProfToken tok = prof_start(CBCT_KERNEL_BACKPROJECT, st);
     switch (zc) {
-    case 8: k_backproject<8><<<grid, block, smem, st>>>(G, gt, out, sx, sy, sz, out2, partials); break;
-    case 4: k_backproject<4><<<grid, block, smem, st>>>(G, gt, out, sx, sy, sz, out2, partials); break;
-    case 2: k_backproject<2><<<grid, block, smem, st>>>(G, gt, out, sx, sy, sz, out2, partials); break;
-    default: k_backproject<1><<<grid, block, smem, st>>>(G, gt, out, sx, sy, sz, out2, partials); break;
+    case 8: k_backproject<8><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials); break;
+    case 4: k_backproject<4><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials); break;
+    case 2: k_backproject<2><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials); break;
+    default: k_backproject<1><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials); break;
     }
     prof_stop(tok, st);
     note_launch();
     return check_cuda(cudaGetLastError(), "backproject launch");
 }
 
-// gt = g * |D - S| per pixel: folds the ray length into the adjoint's input.
-__global__ void k_prescale(GeomDev G, const float *__restrict__ g, float *__restrict__ gt)
+// Prefix sums over imager rows, one column (view k, imager column iu) per thread:
+// ps[k][iu][m] = sum_{iv < m} w(iv) g[k][iv][iu], m = 0..nv, with w = |D - S| if
+// `prescale` (folds the ray length into the adjoint's input) and 1 otherwise. The running
+// sum is FP64 and stored as a float pair (hi, lo = remainder), so differences of two
+// prefixes keep FP32 relative accuracy however long the column.
+__global__ void k_row_prefix(GeomDev G, const float *__restrict__ g, float2 *__restrict__ ps, int prescale)
 {
-    const size_t n = (size_t)G.nviews * G.nv * G.nu;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int iu = (int)(i % G.nu);
-        const int iv = (int)((i / G.nu) % G.nv);
-        const int k = (int)(i / ((size_t)G.nu * G.nv));
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= G.nviews * G.nu) return;
+    const int k = t / G.nu, iu = t - k * G.nu;
+    float dxr = 0.f, dyr = 0.f;
+    if (prescale) {
         const float2 cs = G.cs[k];
-        float dxr, dyr, qx, qy;
+        float qx, qy;
         ray_xy(G, cs.x, cs.y, imager_u(G, iu), dxr, dyr, qx, qy);
-        gt[i] = g[i] * ray_length(dxr, dyr, imager_v(G, iv));
+    }
+    const float *src = g + (size_t)k * G.nv * G.nu + iu;
+    float2 *dst = ps + ((size_t)k * G.nu + iu) * ((size_t)G.nv + 1);
+    double run = 0.0;
+    dst[0] = make_float2(0.0f, 0.0f);
+    for (int iv = 0; iv < G.nv; ++iv) {
+        float val = __ldg(src + (size_t)iv * G.nu);
+        if (prescale) val *= ray_length(dxr, dyr, imager_v(G, iv));
+        run += (double)val;
+        const float hi = (float)run;
+        dst[iv + 1] = make_float2(hi, (float)(run - (double)hi));
     }
 }
 
-cbct_status launch_prescale(const GeomDev &G, const float *g, float *gt, cudaStream_t st)
+cbct_status launch_row_prefix(const GeomDev &G, const float *g, float2 *ps, int prescale, cudaStream_t st)
 {
-    const size_t n = (size_t)G.nviews * G.nv * G.nu;
-    const int threads = 256;
-    const long long want = (long long)((n + threads - 1) / threads);
-    const int blocks = (int)(want < 8LL * device_sm_count() * 8 ? want : 8LL * device_sm_count() * 8);
-    CBCT_TIMED(CBCT_KERNEL_OTHER, st, k_prescale<<<blocks > 0 ? blocks : 1, threads, 0, st>>>(G, g, gt));
-    return check_cuda(cudaGetLastError(), "prescale launch");
+    const int n = G.nviews * G.nu, threads = 128;
+    CBCT_TIMED(CBCT_KERNEL_BACKPROJECT, st,
+               k_row_prefix<<<(n + threads - 1) / threads, threads, 0, st>>>(G, g, ps, prescale));
+    return check_cuda(cudaGetLastError(), "row prefix launch");
 }
 
 } // namespace cbct

@@ -127,10 +127,13 @@ cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long 
                            long long sz, const float *y, float *out, int mode,
                            double *partials, float count_thr, cudaStream_t st);
 int backproject_num_blocks(const GeomDev &G);
-cbct_status launch_backproject(const GeomDev &G, const float *gt, float *out, long long sx,
+// ps: per-(view, imager column) prefix sums over rows of the |D - S|-weighted stack,
+// [n_views][nu][nv + 1] float2 (hi, lo), built by launch_row_prefix.
+cbct_status launch_backproject(const GeomDev &G, const float2 *ps, float *out, long long sx,
                                long long sy, long long sz, float *out2, double *partials,
                                cudaStream_t st);
-cbct_status launch_prescale(const GeomDev &G, const float *g, float *gt, cudaStream_t st);
+cbct_status launch_row_prefix(const GeomDev &G, const float *g, float2 *ps, int prescale,
+                              cudaStream_t st);
 
 cbct_status launch_tf_analyze(int n0, int n1, int n2, const float *f, float *alpha,
                               cudaStream_t st);

@@ -289,9 +289,12 @@ static cbct_status launch_prolong(const Grid3 &cg, const float *fc, const Grid3 
 
 struct Work {
     float *X, *P, *S, *Fa, *Fb, *R, *Q, *alpha;
+    float2 *PS; // row prefix sums of the prescaled residual, input of the adjoint
     double *partials;
     Scalars *sc;
 };
+
+static size_t prefix_elems(const cbct_geometry_desc &d) { return (size_t)d.n_views * d.nu * ((size_t)d.nv + 1); }
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -318,9 +321,10 @@ static size_t work_layout(const cbct_geometry *g, char *base, Work *w)
     float *Fa = (float *)take(4 * N), *Fb = (float *)take(4 * N);
     float *R = (float *)take(4 * M), *Q = (float *)take(4 * M);
     float *alpha = (float *)take(4 * 27 * N);
+    float2 *PS = (float2 *)take(sizeof(float2) * prefix_elems(d));
     double *partials = (double *)take(sizeof(double) * max_partials(g));
     Scalars *sc = (Scalars *)take(sizeof(Scalars));
-    if (w) *w = Work{X, P, S, Fa, Fb, R, Q, alpha, partials, sc};
+    if (w) *w = Work{X, P, S, Fa, Fb, R, Q, alpha, PS, partials, sc};
     return off;
 }
 
@@ -368,7 +372,8 @@ static cbct_status run_cgls(const GeomDev &G, const float *y, float *x, int n_it
     // r = y - P x (stored as |D-S| r); s = P^T r; p = s; gamma = ||s||^2
     TRY(launch_project(G, x, sx, sy, sz, y, w.R, PM_R_PRESCALED, w.partials, 0.0f, st));
     TRY(finalize(w.partials, nbp, w.sc, FIN_RR, st));
-    TRY(launch_backproject(G, w.R, w.S, sx, sy, sz, w.P, w.partials, st));
+    TRY(launch_row_prefix(G, w.R, w.PS, 0, st));
+    TRY(launch_backproject(G, w.PS, w.S, sx, sy, sz, w.P, w.partials, st));
     TRY(finalize(w.partials, nbb, w.sc, FIN_GAMMA, st));
     for (int l = 0; l < n_iter; ++l) {
         // q = P p, alpha = gamma / ||q||^2
@@ -382,7 +387,8 @@ static cbct_status run_cgls(const GeomDev &G, const float *y, float *x, int n_it
         CBCT_TIMED(CBCT_KERNEL_OTHER, st, k_update_r<<<vec_blocks(M), 256, 0, st>>>(w.R, w.Q, w.sc, M));
         TRY(check_cuda(cudaGetLastError(), "update launch"));
         // s = P^T r, beta = ||s||^2 / gamma
-        TRY(launch_backproject(G, w.R, w.S, sx, sy, sz, nullptr, w.partials, st));
+        TRY(launch_row_prefix(G, w.R, w.PS, 0, st));
+        TRY(launch_backproject(G, w.PS, w.S, sx, sy, sz, nullptr, w.partials, st));
         TRY(finalize(w.partials, nbb, w.sc, FIN_BETA, st));
         // x += alpha p; p = s + beta p
         CBCT_TIMED(CBCT_KERNEL_OTHER, st, k_update_xp<<<vec_blocks(N), 256, 0, st>>>(x, w.P, w.S, w.sc, N, 1));
@@ -499,12 +505,11 @@ extern "C" cbct_status cbct_backproject(const cbct_geometry *gc, const float *gi
     if (!gin || !f) return set_error(CBCT_ERR_INVALID_ARG, "backproject: null pointer");
     cbct_geometry *g = const_cast<cbct_geometry *>(gc);
     const GeomDev G = level_geom(g, 0);
-    const size_t M = (size_t)G.nviews * G.nv * G.nu;
-    TRY(ensure_scratch(g, sizeof(float) * M));
+    TRY(ensure_scratch(g, sizeof(float2) * prefix_elems(g->desc)));
     cudaStream_t st = (cudaStream_t)stream;
-    float *gt = g->d_scratch;
-    TRY(launch_prescale(G, gin, gt, st));
-    return launch_backproject(G, gt, f, 1, G.nx, (long long)G.nx * G.ny, nullptr, nullptr, st);
+    float2 *ps = reinterpret_cast<float2 *>(g->d_scratch);
+    TRY(launch_row_prefix(G, gin, ps, 1, st));
+    return launch_backproject(G, ps, f, 1, G.nx, (long long)G.nx * G.ny, nullptr, nullptr, st);
 }
 
 extern "C" cbct_status cbct_tf_analyze(int nx, int ny, int nz, const float *f, float *alpha27, cbct_stream_t stream)
