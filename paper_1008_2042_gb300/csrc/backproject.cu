@@ -50,6 +50,25 @@ __device__ __forceinline__ void straddle_rows(const GeomDev &G, float zp, float 
     hi = (int)floorf(fhi);
 }
 
+// Split of the single row `lo` (if lo == hi) whose ray crosses plane zp inside the column:
+// the tau-length below and above the plane, times the row's weighted value.
+__device__ __forceinline__ void straddle_row(const GeomDev &G, const float *s_invv, const float2 *col, int lo,
+                                             int hi, float zp, float ta, float tb, float &below, float &above)
+{
+    below = 0.0f;
+    above = 0.0f;
+    if (lo == hi && (unsigned)lo < (unsigned)G.nv) {
+        const float iw = s_invv[lo];
+        const float scl = fminf(fmaxf(tau_zplane(zp, iw, G.tc), ta), tb);
+        const float2 Q1 = __ldg(col + lo + 1), Q0 = __ldg(col + lo);
+        const float g = (Q1.x - Q0.x) + (Q1.y - Q0.y);
+        const float wlo = scl - ta, whi = tb - scl;
+        const bool up = iw > 0.0f; // z grows along the ray (v >= 0)
+        below = g * (up ? wlo : whi);
+        above = g * (up ? whi : wlo);
+    }
+}
+
 template <int ZC>
 __global__ void __launch_bounds__(BP_TX *BP_TY)
 k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out, int sx, int sy, int sz,
@@ -79,6 +98,7 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
 #pragma unroll
         for (int z = 0; z <= ZC; ++z) zp[z] = plane_at(iz0 + z, G.dz, G.z0);
         const int nzc = min(ZC, G.nz - iz0); // valid voxels in this chunk
+        const float zabs = fmaxf(fabsf(zp[0]), fabsf(plane_at(iz0 + nzc, G.dz, G.z0)));
         const size_t col_stride = (size_t)G.nv + 1;
 
         for (int k = 0; k < G.nviews; ++k) {
@@ -109,39 +129,66 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
                 const float A = __frcp_rn(G.tc + ta), B = __frcp_rn(G.tc + tb);
                 const float wfull = tb - ta;
                 const float2 *col = ps + ((size_t)k * G.nu + iu) * col_stride;
+                // Plane z = zp is reached by the rows with v between zp*A and zp*B. While that
+                // window is shorter than a row pitch and adjacent planes' windows are apart,
+                // every row crosses at most one plane inside the column (the usual case).
+                const float span = zabs * (A - B) * G.inv_dv;
+                const bool simple = span + 3e-3f < 1.0f && fmaf(G.dz * B, G.inv_dv, -span) > 3e-3f;
                 int lo_p, hi_p;
                 straddle_rows(G, zp[0], A, B, lo_p, hi_p);
+                if (simple) {
+                    float below, above;
+                    straddle_row(G, s_invv, col, lo_p, hi_p, zp[0], ta, tb, below, above);
+                    acc[0] += above;
 #pragma unroll
-                for (int z = 0; z < ZC; ++z) {
-                    if (z >= nzc) break;
-                    int lo_n, hi_n;
-                    straddle_rows(G, zp[z + 1], A, B, lo_n, hi_n);
-                    float a = acc[z];
-                    // rows strictly between the two planes' straddle ranges stay in the slab over
-                    // the whole column: each contributes g * (tb - ta); sum them from the prefix
-                    const int f0 = max(hi_p + 1, 0), f1 = min(lo_n - 1, G.nv - 1);
-                    if (f0 <= f1) {
-                        const float2 P1 = __ldg(col + f1 + 1), P0 = __ldg(col + f0);
-                        a = fmaf(wfull, (P1.x - P0.x) + (P1.y - P0.y), a);
-                    }
-                    // rows that cross a z plane inside the column: exact overlap
-                    const int r0 = max(lo_p, 0), r1 = min(hi_n, G.nv - 1);
-                    for (int iv = r0; iv <= r1; ++iv) {
-                        if (iv == f0 && f0 <= f1) { // already counted
-                            iv = f1;
-                            continue;
+                    for (int z = 0; z < ZC; ++z) {
+                        if (z >= nzc) break;
+                        int lo_n, hi_n;
+                        straddle_rows(G, zp[z + 1], A, B, lo_n, hi_n);
+                        // rows strictly between the planes' windows stay in slab z over the whole
+                        // column: each contributes g * (tb - ta); sum them from the prefix
+                        const int f0 = max(hi_p + 1, 0), f1 = min(lo_n - 1, G.nv - 1);
+                        if (f0 <= f1) {
+                            const float2 P1 = __ldg(col + f1 + 1), P0 = __ldg(col + f0);
+                            acc[z] = fmaf(wfull, (P1.x - P0.x) + (P1.y - P0.y), acc[z]);
                         }
-                        const float iw = s_invv[iv];
-                        const float s0 = tau_zplane(zp[z], iw, G.tc), s1 = tau_zplane(zp[z + 1], iw, G.tc);
-                        const float lo = fmaxf(ta, fminf(s0, s1)), hi = fminf(tb, fmaxf(s0, s1));
-                        if (hi > lo) {
-                            const float2 Q1 = __ldg(col + iv + 1), Q0 = __ldg(col + iv);
-                            a = fmaf((Q1.x - Q0.x) + (Q1.y - Q0.y), hi - lo, a);
-                        }
+                        straddle_row(G, s_invv, col, lo_n, hi_n, zp[z + 1], ta, tb, below, above);
+                        acc[z] += below;
+                        if (z + 1 < ZC && z + 1 < nzc) acc[z + 1] += above;
+                        lo_p = lo_n;
+                        hi_p = hi_n;
                     }
-                    acc[z] = a;
-                    lo_p = lo_n;
-                    hi_p = hi_n;
+                } else {
+#pragma unroll
+                    for (int z = 0; z < ZC; ++z) {
+                        if (z >= nzc) break;
+                        int lo_n, hi_n;
+                        straddle_rows(G, zp[z + 1], A, B, lo_n, hi_n);
+                        float a = acc[z];
+                        const int f0 = max(hi_p + 1, 0), f1 = min(lo_n - 1, G.nv - 1);
+                        if (f0 <= f1) {
+                            const float2 P1 = __ldg(col + f1 + 1), P0 = __ldg(col + f0);
+                            a = fmaf(wfull, (P1.x - P0.x) + (P1.y - P0.y), a);
+                        }
+                        // rows that cross a z plane inside the column: exact overlap
+                        const int r0 = max(lo_p, 0), r1 = min(hi_n, G.nv - 1);
+                        for (int iv = r0; iv <= r1; ++iv) {
+                            if (iv == f0 && f0 <= f1) { // already counted
+                                iv = f1;
+                                continue;
+                            }
+                            const float iw = s_invv[iv];
+                            const float s0 = tau_zplane(zp[z], iw, G.tc), s1 = tau_zplane(zp[z + 1], iw, G.tc);
+                            const float lo = fmaxf(ta, fminf(s0, s1)), hi = fminf(tb, fmaxf(s0, s1));
+                            if (hi > lo) {
+                                const float2 Q1 = __ldg(col + iv + 1), Q0 = __ldg(col + iv);
+                                a = fmaf((Q1.x - Q0.x) + (Q1.y - Q0.y), hi - lo, a);
+                            }
+                        }
+                        acc[z] = a;
+                        lo_p = lo_n;
+                        hi_p = hi_n;
+                    }
                 }
             }
         }

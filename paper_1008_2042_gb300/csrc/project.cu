@@ -206,7 +206,7 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, int sz, const 
     } else if (hit) {
         float sprev = tau_in;
         for (int j = 0; j < nseg; j += SEG_GROUP) {
-            float e[SEG_GROUP], st[SEG_GROUP], val[SEG_GROUP];
+            float e[SEG_GROUP], st[SEG_GROUP];
             int c[SEG_GROUP];
 #pragma unroll
             for (int u = 0; u < SEG_GROUP; u += 4) {
@@ -218,28 +218,42 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, int sz, const 
             st[0] = sprev;
 #pragma unroll
             for (int u = 1; u < SEG_GROUP; ++u) st[u] = e[u - 1];
-            const int koff = kz * sz;
-#pragma unroll
-            for (int u = 0; u < SEG_GROUP; ++u) val[u] = active ? __ldg(f + koff + c[u]) : 0.0f;
-#pragma unroll
-            for (int u = 0; u < SEG_GROUP; ++u) acc = fmaf(val[u], e[u] - st[u], acc);
             const float gend = e[SEG_GROUP - 1];
-            while (tzn < gend) { // the lane crosses z planes inside this group (lane-divergent)
-                const int knew = kz + skz;
-                const bool anew = (unsigned)knew < (unsigned)G.nz;
-                const int noff = knew * sz;
+            const int knew = kz + skz;
+            const bool anew = active && (unsigned)knew < (unsigned)G.nz;
+            // the crossing after tzn, to detect two crossings inside one group
+            const float tz2 = (tzn < gend && anew)
+                                  ? tau_zplane(plane_at(knew + (skz > 0), G.dz, G.z0), inv_v, G.tc) : P_INF;
+            if (!__any_sync(0xffffffffu, tz2 < gend)) {
+                // at most one z crossing per lane: split every column's length at tzn
+                const int koff = kz * sz, noff = knew * sz;
 #pragma unroll
                 for (int u = 0; u < SEG_GROUP; ++u) {
-                    const float part = e[u] - fmaxf(st[u], tzn); // piece of column u past the plane
-                    if (part > 0.0f) {
-                        const float vn = anew ? __ldg(f + noff + c[u]) : 0.0f;
-                        acc = fmaf(vn - val[u], part, acc);
-                        val[u] = vn;
-                    }
+                    const float tcl = fminf(fmaxf(tzn, st[u]), e[u]);
+                    const float wold = tcl - st[u], wnew = e[u] - tcl;
+                    const float vo = active ? __ldg(f + koff + c[u]) : 0.0f;
+                    acc = fmaf(vo, wold, acc);
+                    if (anew && wnew > 0.0f) acc = fmaf(__ldg(f + noff + c[u]), wnew, acc);
                 }
-                kz = knew;
-                active = anew;
-                tzn = anew ? tau_zplane(plane_at(kz + (skz > 0), G.dz, G.z0), inv_v, G.tc) : P_INF;
+                if (tzn < gend) {
+                    kz = knew;
+                    active = anew;
+                    tzn = tz2;
+                }
+            } else {
+                // a lane crosses several z planes in this group: walk it exactly
+#pragma unroll
+                for (int u = 0; u < SEG_GROUP; ++u) {
+                    float sl = st[u];
+                    while (tzn < e[u]) {
+                        if (active) acc = fmaf(__ldg(f + kz * sz + c[u]), tzn - sl, acc);
+                        sl = tzn;
+                        kz += skz;
+                        active = (unsigned)kz < (unsigned)G.nz;
+                        tzn = active ? tau_zplane(plane_at(kz + (skz > 0), G.dz, G.z0), inv_v, G.tc) : P_INF;
+                    }
+                    if (active) acc = fmaf(__ldg(f + kz * sz + c[u]), e[u] - sl, acc);
+                }
             }
             sprev = gend;
         }
