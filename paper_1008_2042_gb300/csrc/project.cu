@@ -64,25 +64,30 @@ static inline int seg_capacity(const GeomDev &G)
     return ((G.nx + G.ny + 3 + SEG_GROUP - 1) / SEG_GROUP + 1) * SEG_GROUP;
 }
 
-// sA, sB (crossing lists), then sEnd and sCol aligned to 16 bytes for vector loads
+// Shared memory of one block: the two crossing lists, then (16-byte aligned) per segment
+// its end tau, its column offset and the packed record used by the walk.
 static inline int seg_offset(const GeomDev &G) { return ((G.nx + G.ny + 2 + 3) / 4) * 4; }
 
 static inline size_t project_smem(const GeomDev &G)
 {
-    return sizeof(float) * (size_t)seg_offset(G) + (sizeof(float) + sizeof(int)) * (size_t)seg_capacity(G);
+    return sizeof(float) * (size_t)seg_offset(G) + (sizeof(float) + sizeof(int) + sizeof(float4)) * (size_t)seg_capacity(G);
 }
 
-// One block per (view, imager column, chunk of rows). Phase 1 (whole block): the
-// transverse Siddon trace of the column's rays — the crossings with the x planes and
-// with the y planes are each increasing in tau, so every crossing's position in the
-// merged order is its own index plus the number of crossings of the other family before
-// it (binary search); this yields the list of (x, y) voxel columns the rays visit and
-// the tau at which each is left. Phase 2 (one lane per imager row): walk that list in
-// groups of SEG_GROUP columns, load all of the group's voxels at the lane's current z
-// slab at once, and correct the few columns in which the lane crosses a z plane.
+// One block per (view, imager column, chunk of rows), volume z-contiguous (sz = 1).
+// Phase 1 (whole block): the transverse Siddon trace of the column's rays — the
+// crossings with the x planes and with the y planes are each increasing in tau, so every
+// crossing's position in the merged order is its own index plus the number of crossings
+// of the other family before it (binary search); this yields the list of (x, y) voxel
+// columns the rays visit and the tau at which each is left. For every segment the block
+// also stores its length, 1 / length and its start relative to its group.
+// Phase 2 (one lane per imager row): walk the list in groups of SEG_GROUP columns. In a
+// group a lane crosses at most one z plane (else an exact sequential walk is used): it
+// reads the voxel pair (kb, kb + 1) around its current and next slab in every column and
+// splits each column's length at its crossing with a saturated FMA. No branch and no
+// integer or compare instruction is spent per column.
 template <int MODE>
 __global__ void __launch_bounds__(512)
-k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, int sz, const float *__restrict__ y,
+k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *__restrict__ y,
           float *__restrict__ out, double *__restrict__ partials, float count_thr)
 {
     extern __shared__ float smem[];
@@ -90,8 +95,9 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, int sz, const 
     float *sA = smem;                      // x-plane crossings, in ray order
     float *sB = sA + (G.nx + 1);           // y-plane crossings
     const int cap = ((G.nx + G.ny + 3 + SEG_GROUP - 1) / SEG_GROUP + 1) * SEG_GROUP;
-    float *sEnd = smem + ((G.nx + G.ny + 2 + 3) / 4) * 4; // tau at which segment j ends (16-B aligned)
-    int *sCol = reinterpret_cast<int *>(sEnd + cap); // voxel-column offset of segment j
+    float *sEnd = smem + ((G.nx + G.ny + 2 + 3) / 4) * 4; // tau at which segment j ends
+    int *sCol = reinterpret_cast<int *>(sEnd + cap);      // voxel-column offset of segment j
+    float4 *sSeg = reinterpret_cast<float4 *>(sCol + cap); // (column bits, length, 1/length, start term)
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int view = blockIdx.x / G.nu;
@@ -170,6 +176,16 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, int sz, const 
         sCol[q] = col0;
     }
     __syncthreads();
+    for (int q = tid; q < cap; q += nthr) {
+        const float e = sEnd[q];
+        const float st = q ? sEnd[q - 1] : tau_in;
+        const int qg = q - q % SEG_GROUP;
+        const float g0 = qg ? sEnd[qg - 1] : tau_in; // start of q's group
+        const float len = e - st;
+        const float ia = len > 0.0f ? __frcp_rn(len) : 0.0f;
+        sSeg[q] = make_float4(__int_as_float(sCol[q]), len, ia, -(st - g0) * ia);
+    }
+    __syncthreads();
 
     // ---- phase 2: per-lane z state ----
     const float v = imager_v(G, iv);
@@ -204,58 +220,59 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, int sz, const 
             s0 = e;
         }
     } else if (hit) {
-        float sprev = tau_in;
+        float g0 = tau_in;
         for (int j = 0; j < nseg; j += SEG_GROUP) {
-            float e[SEG_GROUP], st[SEG_GROUP];
-            int c[SEG_GROUP];
-#pragma unroll
-            for (int u = 0; u < SEG_GROUP; u += 4) {
-                const float4 e4 = *reinterpret_cast<const float4 *>(sEnd + j + u);
-                const int4 c4 = *reinterpret_cast<const int4 *>(sCol + j + u);
-                e[u] = e4.x; e[u + 1] = e4.y; e[u + 2] = e4.z; e[u + 3] = e4.w;
-                c[u] = c4.x; c[u + 1] = c4.y; c[u + 2] = c4.z; c[u + 3] = c4.w;
-            }
-            st[0] = sprev;
-#pragma unroll
-            for (int u = 1; u < SEG_GROUP; ++u) st[u] = e[u - 1];
-            const float gend = e[SEG_GROUP - 1];
+            const float gend = sEnd[j + SEG_GROUP - 1];
             const int knew = kz + skz;
             const bool anew = active && (unsigned)knew < (unsigned)G.nz;
             // the crossing after tzn, to detect two crossings inside one group
             const float tz2 = (tzn < gend && anew)
                                   ? tau_zplane(plane_at(knew + (skz > 0), G.dz, G.z0), inv_v, G.tc) : P_INF;
-            if (!__any_sync(0xffffffffu, tz2 < gend)) {
-                // at most one z crossing per lane: split every column's length at tzn
-                const int koff = kz * sz, noff = knew * sz;
+            if (G.nz >= 2 && !__any_sync(0xffffffffu, tz2 < gend)) {
+                // voxel pair (kb, kb + 1) holding the lane's current slab kz and next slab knew
+                int kb = anew ? min(kz, knew) : (active ? (skz > 0 ? kz - 1 : kz) : 0);
+                kb = min(max(kb, 0), G.nz - 2);
+                const bool lo_old = kb == kz;
+                const float m_lo = ((lo_old && active) || (kb == knew && anew)) ? 1.0f : 0.0f;
+                const float m_hi = ((kb + 1 == kz && active) || (kb + 1 == knew && anew)) ? 1.0f : 0.0f;
+                // the lower voxel takes the part before the crossing if it is the current slab
+                const float sg = lo_old ? 1.0f : -1.0f, hg = lo_old ? 0.0f : 1.0f;
+                const float dt = fminf(tzn, 1e30f) - g0;
+                const float *pb = f + kb;
+                float acc_lo = 0.0f, acc_hi = 0.0f;
 #pragma unroll
                 for (int u = 0; u < SEG_GROUP; ++u) {
-                    const float tcl = fminf(fmaxf(tzn, st[u]), e[u]);
-                    const float wold = tcl - st[u], wnew = e[u] - tcl;
-                    const float vo = active ? __ldg(f + koff + c[u]) : 0.0f;
-                    acc = fmaf(vo, wold, acc);
-                    if (anew && wnew > 0.0f) acc = fmaf(__ldg(f + noff + c[u]), wnew, acc);
+                    const float4 sg4 = sSeg[j + u];
+                    const float *p = pb + __float_as_int(sg4.x);
+                    const float flo = __saturatef(fmaf(sg, fmaf(dt, sg4.z, sg4.w), hg));
+                    const float wlo = sg4.y * flo, whi = sg4.y - wlo;
+                    acc_lo = fmaf(__ldg(p), wlo, acc_lo);
+                    acc_hi = fmaf(__ldg(p + 1), whi, acc_hi);
                 }
+                acc = fmaf(m_lo, acc_lo, fmaf(m_hi, acc_hi, acc));
                 if (tzn < gend) {
                     kz = knew;
                     active = anew;
                     tzn = tz2;
                 }
             } else {
-                // a lane crosses several z planes in this group: walk it exactly
-#pragma unroll
+                // a lane crosses several z planes in this group (or nz = 1): walk it exactly
+#pragma unroll 1
                 for (int u = 0; u < SEG_GROUP; ++u) {
-                    float sl = st[u];
-                    while (tzn < e[u]) {
-                        if (active) acc = fmaf(__ldg(f + kz * sz + c[u]), tzn - sl, acc);
+                    const float e = sEnd[j + u];
+                    const int c = sCol[j + u];
+                    float sl = u ? sEnd[j + u - 1] : g0;
+                    while (tzn < e) {
+                        if (active) acc = fmaf(__ldg(f + kz + c), tzn - sl, acc);
                         sl = tzn;
                         kz += skz;
                         active = (unsigned)kz < (unsigned)G.nz;
                         tzn = active ? tau_zplane(plane_at(kz + (skz > 0), G.dz, G.z0), inv_v, G.tc) : P_INF;
                     }
-                    if (active) acc = fmaf(__ldg(f + kz * sz + c[u]), e[u] - sl, acc);
+                    if (active) acc = fmaf(__ldg(f + kz + c), e - sl, acc);
                 }
             }
-            sprev = gend;
+            g0 = gend;
         }
     }
 
@@ -307,20 +324,21 @@ cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long 
         if (e != cudaSuccess) return check_cuda(e, "project attribute");
         attr_set[mode & 3] = true;
     }
-    const int isx = (int)sx, isy = (int)sy, isz = (int)sz;
+    if (sz != 1) return set_error(CBCT_ERR_INVALID_ARG, "project: the volume must be z-contiguous");
+    const int isx = (int)sx, isy = (int)sy;
     ProfToken tok = prof_start(CBCT_KERNEL_PROJECT, st);
     switch (mode) {
     case PM_PLAIN:
-        k_project<PM_PLAIN><<<grid, rows, smem, st>>>(G, f, isx, isy, isz, y, out, partials, count_thr);
+        k_project<PM_PLAIN><<<grid, rows, smem, st>>>(G, f, isx, isy, y, out, partials, count_thr);
         break;
     case PM_Q_PRESCALED:
-        k_project<PM_Q_PRESCALED><<<grid, rows, smem, st>>>(G, f, isx, isy, isz, y, out, partials, count_thr);
+        k_project<PM_Q_PRESCALED><<<grid, rows, smem, st>>>(G, f, isx, isy, y, out, partials, count_thr);
         break;
     case PM_R_PRESCALED:
-        k_project<PM_R_PRESCALED><<<grid, rows, smem, st>>>(G, f, isx, isy, isz, y, out, partials, count_thr);
+        k_project<PM_R_PRESCALED><<<grid, rows, smem, st>>>(G, f, isx, isy, y, out, partials, count_thr);
         break;
     default:
-        k_project<PM_COUNT><<<grid, rows, smem, st>>>(G, f, isx, isy, isz, y, out, partials, count_thr);
+        k_project<PM_COUNT><<<grid, rows, smem, st>>>(G, f, isx, isy, y, out, partials, count_thr);
         break;
     }
     prof_stop(tok, st);
