@@ -54,6 +54,7 @@ _SIGNATURES = {
     "cbct_geometry_create": [ctypes.POINTER(GeometryDesc), ctypes.POINTER(_vp)],
     "cbct_geometry_destroy": [_vp],
     "cbct_project": [_vp, _vp, _vp, _vp],
+    "cbct_project_static": [_vp, _vp, _vp, _vp],
     "cbct_backproject": [_vp, _vp, _vp, _vp],
     "cbct_tf_analyze": [_i, _i, _i, _vp, _vp, _vp],
     "cbct_tf_synthesize_shrink": [_i, _i, _i, _vp, _f, _i, _vp, _vp],
@@ -188,6 +189,15 @@ def project(geom: Geometry, f: torch.Tensor, out: Optional[torch.Tensor] = None,
         out = torch.empty(geom.proj_shape, dtype=torch.float32, device=f.device)
     _check(load_library().cbct_project(geom.handle, _dev(f, geom.vol_shape, "f"),
                                        _dev(out, geom.proj_shape, "out"), _stream(stream)))
+    return out
+
+
+def project_static(geom: Geometry, f: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """g = P f like project(), using the library's fixed device scratch instead of
+    allocating: for callers that cannot allocate device memory while running. `out` must
+    be supplied (nothing is allocated here either)."""
+    _check(load_library().cbct_project_static(geom.handle, _dev(f, geom.vol_shape, "f"),
+                                              _dev(out, geom.proj_shape, "out"), _stream(stream)))
     return out
 
 

@@ -139,6 +139,9 @@ cbct_status launch_tf_analyze(int n0, int n1, int n2, const float *f, float *alp
                               cudaStream_t st);
 cbct_status launch_tf_synth_shrink(int n0, int n1, int n2, const float *alpha, float mu,
                                    int positivity, float *f, cudaStream_t st);
+// Public x-fastest [nz][ny][nx] <-> internal z-fastest [ny][nx][nz] volume layout.
+cbct_status transpose(const float *in, float *out, int nx, int ny, int nz, bool to_internal,
+                      cudaStream_t st);
 
 } // namespace cbct
 

@@ -159,8 +159,8 @@ __global__ void k_int_to_pub(const float *__restrict__ in, float *__restrict__ o
     }
 }
 
-static cbct_status transpose(const float *in, float *out, int nx, int ny, int nz, bool to_internal,
-                             cudaStream_t st)
+cbct_status transpose(const float *in, float *out, int nx, int ny, int nz, bool to_internal,
+                      cudaStream_t st)
 {
     dim3 grid((nx + 31) / 32, (nz + 31) / 32, ny), block(32, 8);
     if (to_internal) CBCT_TIMED(CBCT_KERNEL_OTHER, st, k_pub_to_int<<<grid, block, 0, st>>>(in, out, nx, ny, nz));
