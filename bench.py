@@ -183,6 +183,32 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def kernel_sources_sha(kernel: str) -> str:
+    """sha256 over the CUDA sources that define a kernel (its .cu file and the internal
+    header), to tie a stored ncu traffic figure to the kernel version it was taken on."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1008_2042_gb300", "csrc")
+    files = {"k_project": "project.cu", "k_backproject": "backproject.cu"}[kernel]
+    h = hashlib.sha256()
+    for name in (files, "cbct_internal.cuh"):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def stored_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None when the
+    kernel's sources changed since that capture (or there is none)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("sources_sha256") != kernel_sources_sha(kernel):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -333,14 +359,14 @@ def run_ours(args):
     ms_p, n_p = ktimes["project"]
     ms_pt, n_pt = ktimes["backproject"]
     if ms_p >= ms_pt:
-        dom, ms_dom, n_dom, upd_dom = "project (P, Siddon column sweep)", ms_p, n_p, updates_P * args.steps
+        dom, kname, ms_dom, n_dom, upd_dom = "project (P, Siddon column sweep)", "k_project", ms_p, n_p, updates_P * args.steps
     else:
-        dom, ms_dom, n_dom, upd_dom = "backproject (exact P^T gather)", ms_pt, n_pt, updates_PT * args.steps
+        dom, kname, ms_dom, n_dom, upd_dom = "backproject (exact P^T gather)", "k_backproject", ms_pt, n_pt, updates_PT * args.steps
     achieved = (upd_dom * OPS_PER_UPDATE / max(n_dom, 1)) / (ms_dom / max(n_dom, 1) / 1e3) / 1e12
     total_kernel_ms = sum(v[0] for v in ktimes.values())
     roofline = {
         "bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-        "frac": achieved / alu_peak, "traffic": None,
+        "frac": achieved / alu_peak, "traffic": stored_traffic(kname),
         "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz (one FP32 op per lane "
                        f"per clock; {OPS_PER_UPDATE} FP32 ops counted per ray-voxel update)",
         "avg_launch_ms": ms_dom / max(n_dom, 1),

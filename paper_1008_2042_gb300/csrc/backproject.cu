@@ -272,7 +272,7 @@ __global__ void k_row_prefix(GeomDev G, const float *__restrict__ g, float2 *__r
 cbct_status launch_row_prefix(const GeomDev &G, const float *g, float2 *ps, int prescale, cudaStream_t st)
 {
     const int n = G.nviews * G.nu, threads = 128;
-    CBCT_TIMED(CBCT_KERNEL_BACKPROJECT, st,
+    CBCT_TIMED(CBCT_KERNEL_OTHER, st,
                k_row_prefix<<<(n + threads - 1) / threads, threads, 0, st>>>(G, g, ps, prescale));
     return check_cuda(cudaGetLastError(), "row prefix launch");
 }
