@@ -50,23 +50,28 @@ __device__ __forceinline__ void straddle_rows(const GeomDev &G, float zp, float 
     hi = (int)floorf(fhi);
 }
 
-// Split of the single row `lo` (if lo == hi) whose ray crosses plane zp inside the column:
-// the tau-length below and above the plane, times the row's weighted value.
-__device__ __forceinline__ void straddle_row(const GeomDev &G, const float *s_invv, const float2 *col, int lo,
-                                             int hi, float zp, float ta, float tb, float &below, float &above)
+// Rows reaching plane zp inside the column lie in the window [a, b) of imager rows (at
+// most one row when the caller's `simple` test holds); a and b are clamped to [0, nv] so
+// that col[a], col[b] are valid prefixes. Returns those prefixes and the straddling row's
+// weighted contributions below and above the plane (zero if the window is empty).
+__device__ __forceinline__ void plane_terms(const GeomDev &G, const float *s_invv, const float2 *col, float zp,
+                                            float A, float B, float ta, float tb, float c0, float c1,
+                                            float2 &Pa, float2 &Pb, float &below, float &above)
 {
-    below = 0.0f;
-    above = 0.0f;
-    if (lo == hi && (unsigned)lo < (unsigned)G.nv) {
-        const float iw = s_invv[lo];
-        const float scl = fminf(fmaxf(tau_zplane(zp, iw, G.tc), ta), tb);
-        const float2 Q1 = __ldg(col + lo + 1), Q0 = __ldg(col + lo);
-        const float g = (Q1.x - Q0.x) + (Q1.y - Q0.y);
-        const float wlo = scl - ta, whi = tb - scl;
-        const bool up = iw > 0.0f; // z grows along the ray (v >= 0)
-        below = g * (up ? wlo : whi);
-        above = g * (up ? whi : wlo);
-    }
+    const float v0 = zp * A, v1 = zp * B;
+    const float nvf = (float)G.nv;
+    const float fa = fminf(fmaxf(fmaf(fminf(v0, v1), G.inv_dv, c0), 0.0f), nvf);
+    const float fb = fminf(fmaxf(fmaf(fmaxf(v0, v1), G.inv_dv, c1), -1.0f), nvf - 1.0f);
+    const int a = ceil_small(fa), b = floor_small(fb) + 1;
+    Pa = __ldg(col + a);
+    Pb = __ldg(col + max(a, b));
+    const float g = (Pb.x - Pa.x) + (Pb.y - Pa.y);
+    const float iw = s_invv[min(a, G.nv - 1)];
+    const float scl = fminf(fmaxf(tau_zplane(zp, iw, G.tc), ta), tb);
+    const float wlo = scl - ta, whi = tb - scl;
+    const bool up = iw > 0.0f; // z grows along the ray (v >= 0)
+    below = g * (up ? wlo : whi);
+    above = g * (up ? whi : wlo);
 }
 
 template <int ZC>
@@ -100,6 +105,7 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
         const int nzc = min(ZC, G.nz - iz0); // valid voxels in this chunk
         const float zabs = fmaxf(fabsf(zp[0]), fabsf(plane_at(iz0 + nzc, G.dz, G.z0)));
         const size_t col_stride = (size_t)G.nv + 1;
+        const float c0 = fmaf(-G.v_first, G.inv_dv, -1e-3f), c1 = fmaf(-G.v_first, G.inv_dv, 1e-3f);
 
         for (int k = 0; k < G.nviews; ++k) {
             const float2 cs = G.cs[k];
@@ -118,15 +124,14 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
             const int iu_hi = min(G.nu - 1, (int)floorf(fmaf(umax - G.u_first, G.inv_du, 1e-3f)));
 
             for (int iu = iu_lo; iu <= iu_hi; ++iu) {
-                float dxr, dyr, qx, qy;
-                ray_xy(G, cs.x, cs.y, imager_u(G, iu), dxr, dyr, qx, qy);
-                const float inv_x = safe_rcp(dxr), inv_y = safe_rcp(dyr);
-                const float t0 = tau_plane(xl, qx, inv_x), t1 = tau_plane(xh, qx, inv_x);
-                const float t2 = tau_plane(yl, qy, inv_y), t3 = tau_plane(yh, qy, inv_y);
+                const float4 r4 = __ldg(G.ray4 + k * G.nu + iu); // (dxr, dyr, qx, qy)
+                const float2 r2 = __ldg(G.ray2 + k * G.nu + iu); // (1/dxr, 1/dyr)
+                const float t0 = tau_plane(xl, r4.z, r2.x), t1 = tau_plane(xh, r4.z, r2.x);
+                const float t2 = tau_plane(yl, r4.w, r2.y), t3 = tau_plane(yh, r4.w, r2.y);
                 const float ta = fmaxf(fminf(t0, t1), fminf(t2, t3));
                 const float tb = fminf(fmaxf(t0, t1), fmaxf(t2, t3));
                 if (!(tb > ta)) continue;
-                const float A = __frcp_rn(G.tc + ta), B = __frcp_rn(G.tc + tb);
+                const float A = __fdividef(1.0f, G.tc + ta), B = __fdividef(1.0f, G.tc + tb);
                 const float wfull = tb - ta;
                 const float2 *col = ps + ((size_t)k * G.nu + iu) * col_stride;
                 // Plane z = zp is reached by the rows with v between zp*A and zp*B. While that
@@ -134,31 +139,26 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
                 // every row crosses at most one plane inside the column (the usual case).
                 const float span = zabs * (A - B) * G.inv_dv;
                 const bool simple = span + 3e-3f < 1.0f && fmaf(G.dz * B, G.inv_dv, -span) > 3e-3f;
-                int lo_p, hi_p;
-                straddle_rows(G, zp[0], A, B, lo_p, hi_p);
                 if (simple) {
+                    // rows strictly between two planes' windows stay in the slab across the
+                    // column (weight tb - ta) and are summed as a prefix difference; the one
+                    // row in a plane's window is split at the plane
+                    float2 Pa, Pb;
                     float below, above;
-                    straddle_row(G, s_invv, col, lo_p, hi_p, zp[0], ta, tb, below, above);
+                    plane_terms(G, s_invv, col, zp[0], A, B, ta, tb, c0, c1, Pa, Pb, below, above);
                     acc[0] += above;
+                    float2 Pprev = Pb;
 #pragma unroll
                     for (int z = 0; z < ZC; ++z) {
                         if (z >= nzc) break;
-                        int lo_n, hi_n;
-                        straddle_rows(G, zp[z + 1], A, B, lo_n, hi_n);
-                        // rows strictly between the planes' windows stay in slab z over the whole
-                        // column: each contributes g * (tb - ta); sum them from the prefix
-                        const int f0 = max(hi_p + 1, 0), f1 = min(lo_n - 1, G.nv - 1);
-                        if (f0 <= f1) {
-                            const float2 P1 = __ldg(col + f1 + 1), P0 = __ldg(col + f0);
-                            acc[z] = fmaf(wfull, (P1.x - P0.x) + (P1.y - P0.y), acc[z]);
-                        }
-                        straddle_row(G, s_invv, col, lo_n, hi_n, zp[z + 1], ta, tb, below, above);
-                        acc[z] += below;
+                        plane_terms(G, s_invv, col, zp[z + 1], A, B, ta, tb, c0, c1, Pa, Pb, below, above);
+                        acc[z] = fmaf(wfull, (Pa.x - Pprev.x) + (Pa.y - Pprev.y), acc[z]) + below;
                         if (z + 1 < ZC && z + 1 < nzc) acc[z + 1] += above;
-                        lo_p = lo_n;
-                        hi_p = hi_n;
+                        Pprev = Pb;
                     }
                 } else {
+                    int lo_p, hi_p;
+                    straddle_rows(G, zp[0], A, B, lo_p, hi_p);
 #pragma unroll
                     for (int z = 0; z < ZC; ++z) {
                         if (z >= nzc) break;

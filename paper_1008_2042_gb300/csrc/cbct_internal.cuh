@@ -32,6 +32,8 @@ struct GeomDev {
     float sad, sdd;
     float tc;               // sad / sdd: ray parameter of the isocentre plane
     const float2 *cs;       // (cos t_k, sin t_k) per view, device memory
+    const float4 *ray4;     // per (view, imager column): (dxr, dyr, qx, qy) of ray_xy
+    const float2 *ray2;     // per (view, imager column): (1/dxr, 1/dyr) of safe_rcp
 };
 
 // Rays are parametrised as X(tau) = Q + tau * d, d = D - S (source to pixel centre) and
@@ -67,6 +69,11 @@ __device__ __forceinline__ float tau_zplane(float p, float inv_v, float tc) { re
 
 __device__ __forceinline__ float imager_u(const GeomDev &G, int iu) { return fmaf((float)iu, G.du, G.u_first); }
 __device__ __forceinline__ float imager_v(const GeomDev &G, int iv) { return fmaf((float)iv, G.dv, G.v_first); }
+
+// Exact ceil / floor of |x| < 2^22 through the FP adder (no conversion instruction):
+// adding 1.5 * 2^23 with rounding up / down leaves the integer in the low mantissa bits.
+__device__ __forceinline__ int ceil_small(float x) { return __float_as_int(__fadd_ru(x, 12582912.0f)) - 0x4B400000; }
+__device__ __forceinline__ int floor_small(float x) { return __float_as_int(__fadd_rd(x, 12582912.0f)) - 0x4B400000; }
 
 // Length of ray (d) per unit tau: |D - S|.
 __device__ __forceinline__ float ray_length(float dxr, float dyr, float v)
@@ -151,6 +158,8 @@ struct cbct_geometry {
     double *angles;          // host copy
     int device;
     float2 *d_cs;            // per-view (cos, sin)
+    float4 *d_ray4;          // per (view, imager column) transverse ray (ray_xy)
+    float2 *d_ray2;          // per (view, imager column) reciprocal directions
     float *d_scratch;        // public project/backproject scratch (lazily allocated)
     size_t scratch_bytes;
     void *d_ws;              // reconstruction workspace (lazily allocated)

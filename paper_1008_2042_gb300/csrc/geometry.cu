@@ -129,7 +129,23 @@ GeomDev level_geom(const cbct_geometry *g, int level)
     G.sdd = (float)d.sdd;
     G.tc = (float)(d.sad / d.sdd);
     G.cs = g->d_cs;
+    G.ray4 = g->d_ray4;
+    G.ray2 = g->d_ray2;
     return G;
+}
+
+// Transverse ray of every (view, imager column), computed once per geometry with the
+// same expressions the projector evaluates per block (so the values are identical).
+__global__ void k_ray_table(GeomDev G, float4 *ray4, float2 *ray2)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= G.nviews * G.nu) return;
+    const int k = t / G.nu, iu = t - k * G.nu;
+    const float2 cs = G.cs[k];
+    float dxr, dyr, qx, qy;
+    ray_xy(G, cs.x, cs.y, imager_u(G, iu), dxr, dyr, qx, qy);
+    ray4[t] = make_float4(dxr, dyr, qx, qy);
+    ray2[t] = make_float2(safe_rcp(dxr), safe_rcp(dyr));
 }
 
 cbct_status ensure_scratch(cbct_geometry *g, size_t bytes)
@@ -238,12 +254,24 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct
     }
     g->desc.angles = g->angles;
     cudaGetDevice(&g->device);
+    const size_t nrays = (size_t)d.n_views * d.nu;
     cudaError_t e = cudaMalloc(&g->d_cs, sizeof(float2) * d.n_views);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_ray4, sizeof(float4) * nrays);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_ray2, sizeof(float2) * nrays);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_cs, h_cs, sizeof(float2) * d.n_views, cudaMemcpyHostToDevice);
     free(h_cs);
+    if (e == cudaSuccess) {
+        const GeomDev G = level_geom(g, 0);
+        k_ray_table<<<(unsigned)((nrays + 127) / 128), 128>>>(G, g->d_ray4, g->d_ray2);
+        note_launch();
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
     if (e != cudaSuccess) {
         cbct_status st = check_cuda(e, "geometry_create");
         cudaFree(g->d_cs);
+        cudaFree(g->d_ray4);
+        cudaFree(g->d_ray2);
         free(g->angles);
         free(g);
         return st;
@@ -257,6 +285,8 @@ extern "C" cbct_status cbct_geometry_destroy(cbct_geometry *g)
     if (!g) return CBCT_OK;
     cudaError_t e = cudaDeviceSynchronize();
     cudaFree(g->d_cs);
+    cudaFree(g->d_ray4);
+    cudaFree(g->d_ray2);
     cudaFree(g->d_scratch);
     cudaFree(g->d_ws);
     free(g->angles);

@@ -35,7 +35,7 @@ int project_num_blocks(const GeomDev &G)
 }
 
 // Number of column segments a lane processes per unrolled group.
-constexpr int SEG_GROUP = 8;
+constexpr int SEG_GROUP = 16;
 
 __device__ __forceinline__ int lower_count(const float *a, int n, float t) // # a[i] < t
 {
