@@ -68,10 +68,25 @@ static inline int seg_capacity(const GeomDev &G)
 // its end tau, its column offset and the packed record used by the walk.
 static inline int seg_offset(const GeomDev &G) { return ((G.nx + G.ny + 2 + 3) / 4) * 4; }
 
+// z-lines of one group of columns, staged in shared memory: [z][column in group], the
+// column stride padded to an odd number of floats so the staging writes do not conflict.
+constexpr int LINE_PITCH = SEG_GROUP + 1;
+
 static inline size_t project_smem(const GeomDev &G)
 {
-    return sizeof(float) * (size_t)seg_offset(G) + (sizeof(float) + sizeof(int) + sizeof(float4)) * (size_t)seg_capacity(G);
+    return sizeof(float) * (size_t)seg_offset(G) + (sizeof(float) + sizeof(int) + sizeof(float4)) * (size_t)seg_capacity(G) +
+           sizeof(float) * 2 * (size_t)G.nz * LINE_PITCH;
 }
+
+size_t project_smem_bytes(const GeomDev &G) { return project_smem(G); }
+
+__device__ __forceinline__ void cp_async4(float *smem_dst, const float *gsrc)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // One block per (view, imager column, chunk of rows), volume z-contiguous (sz = 1).
 // Phase 1 (whole block): the transverse Siddon trace of the column's rays — the
@@ -98,6 +113,7 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
     float *sEnd = smem + ((G.nx + G.ny + 2 + 3) / 4) * 4; // tau at which segment j ends
     int *sCol = reinterpret_cast<int *>(sEnd + cap);      // voxel-column offset of segment j
     float4 *sSeg = reinterpret_cast<float4 *>(sCol + cap); // (column bits, length, 1/length, start term)
+    float *sLine = reinterpret_cast<float *>(sSeg + cap);  // two staged groups of column z-lines
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int view = blockIdx.x / G.nu;
@@ -220,8 +236,39 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
             s0 = e;
         }
     } else if (hit) {
+        // Stage the z-lines of each group of columns into shared memory one group ahead
+        // (cp.async), then let every lane read its voxel pair there.
+        const int nchunk = (nseg + SEG_GROUP - 1) / SEG_GROUP;
+        const int line_elems = SEG_GROUP * G.nz;
+        const int u0 = tid / G.nz, k0 = tid - u0 * G.nz;
+        const int du = nthr / G.nz, dk = nthr - du * G.nz;
+        auto fill = [&](int chunk, int buf) {
+            float *dst = sLine + buf * G.nz * LINE_PITCH;
+            const float4 *seg = sSeg + chunk * SEG_GROUP;
+            int u = u0, k = k0;
+            for (int idx = tid; idx < line_elems; idx += nthr) {
+                cp_async4(dst + k * LINE_PITCH + u, f + __float_as_int(seg[u].x) + k);
+                k += dk;
+                u += du;
+                if (k >= G.nz) {
+                    k -= G.nz;
+                    ++u;
+                }
+            }
+            cp_async_commit();
+        };
+        fill(0, 0);
         float g0 = tau_in;
-        for (int j = 0; j < nseg; j += SEG_GROUP) {
+        for (int ch = 0; ch < nchunk; ++ch) {
+            const int j = ch * SEG_GROUP;
+            if (ch + 1 < nchunk) {
+                fill(ch + 1, (ch + 1) & 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            const float *lines = sLine + (ch & 1) * G.nz * LINE_PITCH;
             const float gend = sEnd[j + SEG_GROUP - 1];
             const int knew = kz + skz;
             const bool anew = active && (unsigned)knew < (unsigned)G.nz;
@@ -238,16 +285,15 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
                 // the lower voxel takes the part before the crossing if it is the current slab
                 const float sg = lo_old ? 1.0f : -1.0f, hg = lo_old ? 0.0f : 1.0f;
                 const float dt = fminf(tzn, 1e30f) - g0;
-                const float *pb = f + kb;
+                const float *base = lines + kb * LINE_PITCH;
                 float acc_lo = 0.0f, acc_hi = 0.0f;
 #pragma unroll
                 for (int u = 0; u < SEG_GROUP; ++u) {
                     const float4 sg4 = sSeg[j + u];
-                    const float *p = pb + __float_as_int(sg4.x);
                     const float flo = __saturatef(fmaf(sg, fmaf(dt, sg4.z, sg4.w), hg));
                     const float wlo = sg4.y * flo, whi = sg4.y - wlo;
-                    acc_lo = fmaf(__ldg(p), wlo, acc_lo);
-                    acc_hi = fmaf(__ldg(p + 1), whi, acc_hi);
+                    acc_lo = fmaf(base[u], wlo, acc_lo);
+                    acc_hi = fmaf(base[LINE_PITCH + u], whi, acc_hi);
                 }
                 acc = fmaf(m_lo, acc_lo, fmaf(m_hi, acc_hi, acc));
                 if (tzn < gend) {
@@ -260,19 +306,19 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
 #pragma unroll 1
                 for (int u = 0; u < SEG_GROUP; ++u) {
                     const float e = sEnd[j + u];
-                    const int c = sCol[j + u];
                     float sl = u ? sEnd[j + u - 1] : g0;
                     while (tzn < e) {
-                        if (active) acc = fmaf(__ldg(f + kz + c), tzn - sl, acc);
+                        if (active) acc = fmaf(lines[kz * LINE_PITCH + u], tzn - sl, acc);
                         sl = tzn;
                         kz += skz;
                         active = (unsigned)kz < (unsigned)G.nz;
                         tzn = active ? tau_zplane(plane_at(kz + (skz > 0), G.dz, G.z0), inv_v, G.tc) : P_INF;
                     }
-                    if (active) acc = fmaf(__ldg(f + kz + c), e - sl, acc);
+                    if (active) acc = fmaf(lines[kz * LINE_PITCH + u], e - sl, acc);
                 }
             }
             g0 = gend;
+            __syncthreads();
         }
     }
 
@@ -314,13 +360,15 @@ cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long 
     const int rows = proj_rows(G);
     dim3 grid((unsigned)(G.nviews * G.nu), (unsigned)((G.nv + rows - 1) / rows));
     const size_t smem = project_smem(G);
+    if (smem > 200 * 1024)
+        return set_error(CBCT_ERR_UNSUPPORTED, "project: grid too large for the projector's shared memory (nx + ny and nz)");
     static bool attr_set[4] = {false, false, false, false};
     if (!attr_set[mode & 3]) {
         const void *fn = mode == PM_PLAIN ? (const void *)k_project<PM_PLAIN>
                        : mode == PM_Q_PRESCALED ? (const void *)k_project<PM_Q_PRESCALED>
                        : mode == PM_R_PRESCALED ? (const void *)k_project<PM_R_PRESCALED>
                                                 : (const void *)k_project<PM_COUNT>;
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return check_cuda(e, "project attribute");
         attr_set[mode & 3] = true;
     }
