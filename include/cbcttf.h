@@ -60,7 +60,7 @@ typedef struct {
     double du, dv;           /* pixel pitch (mm), > 0 */
     double u_off, v_off;     /* imager offset from the central ray (mm) */
     double sad, sdd;         /* source-to-axis and source-to-imager distance (mm) */
-    int n_views;             /* number of views, >= 1 */
+    int n_views;             /* number of views, 1 .. 65535 */
     const double *angles;    /* host array of n_views angles (rad); NULL = 2 pi k / n_views */
 } cbct_geometry_desc;
 

@@ -240,27 +240,46 @@ cbct_status launch_backproject(const GeomDev &G, const float2 *ps, float *out, l
     return check_cuda(cudaGetLastError(), "backproject launch");
 }
 
-// Prefix sums over imager rows, one column (view k, imager column iu) per thread:
+// Prefix sums over imager rows of every (view k, imager column iu):
 // ps[k][iu][m] = sum_{iv < m} w(iv) g[k][iv][iu], m = 0..nv, with w = |D - S| if
-// `prescale` (folds the ray length into the adjoint's input) and 1 otherwise. The running
-// sum is FP64 and stored as a float pair (hi, lo = remainder), so differences of two
-// prefixes keep FP32 relative accuracy however long the column.
-__global__ void k_row_prefix(GeomDev G, const float *__restrict__ g, float2 *__restrict__ ps, int prescale)
+// `prescale` (folds the ray length into the adjoint's input) and 1 otherwise. Sums are
+// accumulated in FP64 and stored as a float pair (hi, lo = remainder), so differences of
+// two prefixes keep FP32 relative accuracy however long the column. A block covers 32
+// columns (lanes, coalesced reads) of one view; its 16 warps take consecutive row chunks:
+// pass 1 sums each chunk, the chunk offsets come from shared memory, pass 2 writes.
+constexpr int PREFIX_WARPS = 16;
+
+__global__ void __launch_bounds__(32 * PREFIX_WARPS)
+k_row_prefix(GeomDev G, const float *__restrict__ g, float2 *__restrict__ ps, int prescale)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= G.nviews * G.nu) return;
-    const int k = t / G.nu, iu = t - k * G.nu;
+    __shared__ double s_tot[PREFIX_WARPS][32];
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int k = blockIdx.y, iu = blockIdx.x * 32 + lane;
+    const bool ok = iu < G.nu;
+    const int chunk = (G.nv + PREFIX_WARPS - 1) / PREFIX_WARPS;
+    const int r0 = min(G.nv, w * chunk), r1 = min(G.nv, r0 + chunk);
     float dxr = 0.f, dyr = 0.f;
-    if (prescale) {
-        const float2 cs = G.cs[k];
-        float qx, qy;
-        ray_xy(G, cs.x, cs.y, imager_u(G, iu), dxr, dyr, qx, qy);
+    if (prescale && ok) {
+        const float4 r4 = __ldg(G.ray4 + k * G.nu + iu);
+        dxr = r4.x;
+        dyr = r4.y;
     }
     const float *src = g + (size_t)k * G.nv * G.nu + iu;
-    float2 *dst = ps + ((size_t)k * G.nu + iu) * ((size_t)G.nv + 1);
+    double t = 0.0;
+    if (ok)
+        for (int iv = r0; iv < r1; ++iv) {
+            float val = __ldg(src + (size_t)iv * G.nu);
+            if (prescale) val *= ray_length(dxr, dyr, imager_v(G, iv));
+            t += (double)val;
+        }
+    s_tot[w][lane] = t;
+    __syncthreads();
     double run = 0.0;
-    dst[0] = make_float2(0.0f, 0.0f);
-    for (int iv = 0; iv < G.nv; ++iv) {
+    for (int c = 0; c < w; ++c) run += s_tot[c][lane];
+    if (!ok) return;
+    float2 *dst = ps + ((size_t)k * G.nu + iu) * ((size_t)G.nv + 1);
+    if (w == 0) dst[0] = make_float2(0.0f, 0.0f);
+    for (int iv = r0; iv < r1; ++iv) {
         float val = __ldg(src + (size_t)iv * G.nu);
         if (prescale) val *= ray_length(dxr, dyr, imager_v(G, iv));
         run += (double)val;
@@ -271,9 +290,8 @@ __global__ void k_row_prefix(GeomDev G, const float *__restrict__ g, float2 *__r
 
 cbct_status launch_row_prefix(const GeomDev &G, const float *g, float2 *ps, int prescale, cudaStream_t st)
 {
-    const int n = G.nviews * G.nu, threads = 128;
-    CBCT_TIMED(CBCT_KERNEL_OTHER, st,
-               k_row_prefix<<<(n + threads - 1) / threads, threads, 0, st>>>(G, g, ps, prescale));
+    dim3 grid((G.nu + 31) / 32, G.nviews), block(32, PREFIX_WARPS);
+    CBCT_TIMED(CBCT_KERNEL_OTHER, st, k_row_prefix<<<grid, block, 0, st>>>(G, g, ps, prescale));
     return check_cuda(cudaGetLastError(), "row prefix launch");
 }
 

@@ -216,6 +216,7 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct
     if (d.nx < 1 || d.ny < 1 || d.nz < 1 || d.nu < 1 || d.nv < 1 || d.n_views < 1)
         return set_error(CBCT_ERR_INVALID_ARG, "geometry_create: sizes must be >= 1");
     if (d.nv > 8192) return set_error(CBCT_ERR_INVALID_ARG, "geometry_create: nv > 8192");
+    if (d.n_views > 65535) return set_error(CBCT_ERR_INVALID_ARG, "geometry_create: n_views > 65535");
     if (d.nx > 65535 || d.ny > 65535 || d.nz > 65535 || d.nx + d.ny > 4096 || d.nz > 1024)
         return set_error(CBCT_ERR_INVALID_ARG, "geometry_create: need nx + ny <= 4096 and nz <= 1024");
     if (!(d.dx > 0 && d.dy > 0 && d.dz > 0 && d.du > 0 && d.dv > 0))

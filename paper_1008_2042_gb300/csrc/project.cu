@@ -19,7 +19,7 @@
 
 namespace cbct {
 
-constexpr int PROJ_ROWS = 512; // at most this many imager rows per block
+constexpr int PROJ_ROWS = 384; // at most this many imager rows per block
 constexpr float P_INF = 3.0e38f;
 
 static inline int proj_rows(const GeomDev &G)
@@ -68,14 +68,16 @@ static inline int seg_capacity(const GeomDev &G)
 // its end tau, its column offset and the packed record used by the walk.
 static inline int seg_offset(const GeomDev &G) { return ((G.nx + G.ny + 2 + 3) / 4) * 4; }
 
-// z-lines of one group of columns, staged in shared memory: [z][column in group], the
-// column stride padded to an odd number of floats so the staging writes do not conflict.
+// z-lines of one group of columns, staged in shared memory as adjacent-voxel pairs
+// (f[k], f[k+1]) indexed [k][column in group], the column pitch odd to spread banks.
 constexpr int LINE_PITCH = SEG_GROUP + 1;
+
+static inline int line_pairs(const GeomDev &G) { return G.nz > 1 ? G.nz - 1 : 1; }
 
 static inline size_t project_smem(const GeomDev &G)
 {
     return sizeof(float) * (size_t)seg_offset(G) + (sizeof(float) + sizeof(int) + sizeof(float4)) * (size_t)seg_capacity(G) +
-           sizeof(float) * 2 * (size_t)G.nz * LINE_PITCH;
+           sizeof(float2) * 2 * (size_t)line_pairs(G) * LINE_PITCH;
 }
 
 size_t project_smem_bytes(const GeomDev &G) { return project_smem(G); }
@@ -101,19 +103,20 @@ template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile(
 // splits each column's length at its crossing with a saturated FMA. No branch and no
 // integer or compare instruction is spent per column.
 template <int MODE>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(PROJ_ROWS, 3)
 k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *__restrict__ y,
           float *__restrict__ out, double *__restrict__ partials, float count_thr)
 {
     extern __shared__ float smem[];
-    __shared__ double s_warp[16];
+    __shared__ double s_warp[PROJ_ROWS / 32];
     float *sA = smem;                      // x-plane crossings, in ray order
     float *sB = sA + (G.nx + 1);           // y-plane crossings
     const int cap = ((G.nx + G.ny + 3 + SEG_GROUP - 1) / SEG_GROUP + 1) * SEG_GROUP;
     float *sEnd = smem + ((G.nx + G.ny + 2 + 3) / 4) * 4; // tau at which segment j ends
     int *sCol = reinterpret_cast<int *>(sEnd + cap);      // voxel-column offset of segment j
     float4 *sSeg = reinterpret_cast<float4 *>(sCol + cap); // (column bits, length, 1/length, start term)
-    float *sLine = reinterpret_cast<float *>(sSeg + cap);  // two staged groups of column z-lines
+    float2 *sPair = reinterpret_cast<float2 *>(sSeg + cap); // two staged groups of z-line pairs
+    const int npair = G.nz > 1 ? G.nz - 1 : 1;
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int view = blockIdx.x / G.nu;
@@ -243,11 +246,13 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
         const int u0 = tid / G.nz, k0 = tid - u0 * G.nz;
         const int du = nthr / G.nz, dk = nthr - du * G.nz;
         auto fill = [&](int chunk, int buf) {
-            float *dst = sLine + buf * G.nz * LINE_PITCH;
+            float2 *dst = sPair + buf * npair * LINE_PITCH;
             const float4 *seg = sSeg + chunk * SEG_GROUP;
             int u = u0, k = k0;
             for (int idx = tid; idx < line_elems; idx += nthr) {
-                cp_async4(dst + k * LINE_PITCH + u, f + __float_as_int(seg[u].x) + k);
+                const float *src = f + __float_as_int(seg[u].x) + k;
+                if (k < npair) cp_async4(&dst[k * LINE_PITCH + u].x, src);   // first of pair k
+                if (k >= 1) cp_async4(&dst[(k - 1) * LINE_PITCH + u].y, src); // second of pair k - 1
                 k += dk;
                 u += du;
                 if (k >= G.nz) {
@@ -268,7 +273,7 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
                 cp_async_wait<0>();
             }
             __syncthreads();
-            const float *lines = sLine + (ch & 1) * G.nz * LINE_PITCH;
+            const float2 *pairs = sPair + (ch & 1) * npair * LINE_PITCH;
             const float gend = sEnd[j + SEG_GROUP - 1];
             const int knew = kz + skz;
             const bool anew = active && (unsigned)knew < (unsigned)G.nz;
@@ -285,15 +290,16 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
                 // the lower voxel takes the part before the crossing if it is the current slab
                 const float sg = lo_old ? 1.0f : -1.0f, hg = lo_old ? 0.0f : 1.0f;
                 const float dt = fminf(tzn, 1e30f) - g0;
-                const float *base = lines + kb * LINE_PITCH;
+                const float2 *base = pairs + kb * LINE_PITCH;
                 float acc_lo = 0.0f, acc_hi = 0.0f;
 #pragma unroll
                 for (int u = 0; u < SEG_GROUP; ++u) {
                     const float4 sg4 = sSeg[j + u];
                     const float flo = __saturatef(fmaf(sg, fmaf(dt, sg4.z, sg4.w), hg));
                     const float wlo = sg4.y * flo, whi = sg4.y - wlo;
-                    acc_lo = fmaf(base[u], wlo, acc_lo);
-                    acc_hi = fmaf(base[LINE_PITCH + u], whi, acc_hi);
+                    const float2 v = base[u];
+                    acc_lo = fmaf(v.x, wlo, acc_lo);
+                    acc_hi = fmaf(v.y, whi, acc_hi);
                 }
                 acc = fmaf(m_lo, acc_lo, fmaf(m_hi, acc_hi, acc));
                 if (tzn < gend) {
@@ -308,13 +314,15 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
                     const float e = sEnd[j + u];
                     float sl = u ? sEnd[j + u - 1] : g0;
                     while (tzn < e) {
-                        if (active) acc = fmaf(lines[kz * LINE_PITCH + u], tzn - sl, acc);
+                        if (active) acc = fmaf(kz < npair ? pairs[kz * LINE_PITCH + u].x : pairs[(kz - 1) * LINE_PITCH + u].y,
+                                               tzn - sl, acc);
                         sl = tzn;
                         kz += skz;
                         active = (unsigned)kz < (unsigned)G.nz;
                         tzn = active ? tau_zplane(plane_at(kz + (skz > 0), G.dz, G.z0), inv_v, G.tc) : P_INF;
                     }
-                    if (active) acc = fmaf(lines[kz * LINE_PITCH + u], e - sl, acc);
+                    if (active) acc = fmaf(kz < npair ? pairs[kz * LINE_PITCH + u].x : pairs[(kz - 1) * LINE_PITCH + u].y,
+                                           e - sl, acc);
                 }
             }
             g0 = gend;
