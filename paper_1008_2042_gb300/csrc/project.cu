@@ -19,18 +19,21 @@
 
 namespace cbct {
 
-constexpr int PROJ_ROWS = 384; // at most this many imager rows per block
+constexpr int PROJ_THREADS = 192; // threads per block; each thread walks two imager rows
 constexpr float P_INF = 3.0e38f;
 
-static inline int proj_rows(const GeomDev &G)
+// threads of a block (a multiple of 32, every lane present for warp votes) and the imager
+// rows one block covers (two per thread)
+static inline int proj_threads(const GeomDev &G)
 {
-    int r = ((G.nv + 31) / 32) * 32;
-    return r < PROJ_ROWS ? r : PROJ_ROWS;
+    const int rows = G.nv < 2 * PROJ_THREADS ? G.nv : 2 * PROJ_THREADS;
+    const int t = (((rows + 1) / 2 + 31) / 32) * 32;
+    return t < PROJ_THREADS ? t : PROJ_THREADS;
 }
 
 int project_num_blocks(const GeomDev &G)
 {
-    int rows = proj_rows(G);
+    const int rows = 2 * proj_threads(G);
     return G.nviews * G.nu * ((G.nv + rows - 1) / rows);
 }
 
@@ -103,12 +106,12 @@ template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile(
 // splits each column's length at its crossing with a saturated FMA. No branch and no
 // integer or compare instruction is spent per column.
 template <int MODE>
-__global__ void __launch_bounds__(PROJ_ROWS, 3)
+__global__ void __launch_bounds__(PROJ_THREADS, 4)
 k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *__restrict__ y,
           float *__restrict__ out, double *__restrict__ partials, float count_thr)
 {
     extern __shared__ float smem[];
-    __shared__ double s_warp[PROJ_ROWS / 32];
+    __shared__ double s_warp[PROJ_THREADS / 32];
     float *sA = smem;                      // x-plane crossings, in ray order
     float *sB = sA + (G.nx + 1);           // y-plane crossings
     const int cap = ((G.nx + G.ny + 3 + SEG_GROUP - 1) / SEG_GROUP + 1) * SEG_GROUP;
@@ -121,8 +124,6 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int view = blockIdx.x / G.nu;
     const int iu = blockIdx.x - view * G.nu;
-    const int iv = blockIdx.y * blockDim.x + tid;
-    const bool row_ok = iv < G.nv;
 
     // ---- transverse ray, shared by every row ----
     const float2 cs = G.cs[view];
@@ -206,41 +207,53 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
     }
     __syncthreads();
 
-    // ---- phase 2: per-lane z state ----
-    const float v = imager_v(G, iv);
-    const float inv_v = v != 0.0f ? __frcp_rn(v) : 1e30f;
-    const int skz = v >= 0.0f ? 1 : -1;
-    int kz = (int)floorf((v * (G.tc + tau_in) - G.z0) / G.dz);
-    bool active = hit && row_ok && kz >= 0 && kz < G.nz;
-    float tzn = active ? tau_zplane(plane_at(kz + (skz > 0), G.dz, G.z0), inv_v, G.tc) : P_INF;
-    if (active && tzn <= tau_in) { // the entry point already lies past that plane
-        kz += skz;
-        active = (unsigned)kz < (unsigned)G.nz;
-        tzn = active ? tau_zplane(plane_at(kz + (skz > 0), G.dz, G.z0), inv_v, G.tc) : P_INF;
+    // ---- phase 2: per-row z state (two rows per thread: iv[0] and iv[1] = iv[0] + nthr) ----
+    constexpr int R = 2;
+    int iv[R], skz[R], kz[R];
+    float inv_v[R], tzn[R], L[R], acc[R];
+    bool ok[R], active[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        iv[r] = blockIdx.y * (R * nthr) + r * nthr + tid;
+        ok[r] = iv[r] < G.nv;
+        const float v = imager_v(G, iv[r]);
+        inv_v[r] = v != 0.0f ? __frcp_rn(v) : 1e30f;
+        skz[r] = v >= 0.0f ? 1 : -1;
+        kz[r] = (int)floorf((v * (G.tc + tau_in) - G.z0) / G.dz);
+        active[r] = hit && ok[r] && kz[r] >= 0 && kz[r] < G.nz;
+        tzn[r] = active[r] ? tau_zplane(plane_at(kz[r] + (skz[r] > 0), G.dz, G.z0), inv_v[r], G.tc) : P_INF;
+        if (active[r] && tzn[r] <= tau_in) { // the entry point already lies past that plane
+            kz[r] += skz[r];
+            active[r] = (unsigned)kz[r] < (unsigned)G.nz;
+            tzn[r] = active[r] ? tau_zplane(plane_at(kz[r] + (skz[r] > 0), G.dz, G.z0), inv_v[r], G.tc) : P_INF;
+        }
+        L[r] = ray_length(dxr, dyr, v);
+        acc[r] = 0.0f;
     }
-    const float L = ray_length(dxr, dyr, v);
 
-    float acc = 0.0f;
     int cnt = 0;
     if (hit && MODE == PM_COUNT) {
-        const float thr_tau = count_thr / L;
-        float s0 = tau_in;
-        for (int j = 0; j < nseg; ++j) {
-            const float e = sEnd[j];
-            float sl = s0;
-            while (tzn < e) {
-                cnt += (tzn - sl) > thr_tau;
-                sl = tzn;
-                kz += skz;
-                active = (unsigned)kz < (unsigned)G.nz;
-                tzn = active ? tau_zplane(plane_at(kz + (skz > 0), G.dz, G.z0), inv_v, G.tc) : P_INF;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float thr_tau = count_thr / L[r];
+            float s0 = tau_in;
+            for (int j = 0; j < nseg; ++j) {
+                const float e = sEnd[j];
+                float sl = s0;
+                while (tzn[r] < e) {
+                    cnt += (tzn[r] - sl) > thr_tau;
+                    sl = tzn[r];
+                    kz[r] += skz[r];
+                    active[r] = (unsigned)kz[r] < (unsigned)G.nz;
+                    tzn[r] = active[r] ? tau_zplane(plane_at(kz[r] + (skz[r] > 0), G.dz, G.z0), inv_v[r], G.tc) : P_INF;
+                }
+                if (active[r]) cnt += (e - sl) > thr_tau;
+                s0 = e;
             }
-            if (active) cnt += (e - sl) > thr_tau;
-            s0 = e;
         }
     } else if (hit) {
         // Stage the z-lines of each group of columns into shared memory one group ahead
-        // (cp.async), then let every lane read its voxel pair there.
+        // (cp.async), then let every row read its voxel pair there.
         const int nchunk = (nseg + SEG_GROUP - 1) / SEG_GROUP;
         const int line_elems = SEG_GROUP * G.nz;
         const int u0 = tid / G.nz, k0 = tid - u0 * G.nz;
@@ -275,54 +288,83 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
             __syncthreads();
             const float2 *pairs = sPair + (ch & 1) * npair * LINE_PITCH;
             const float gend = sEnd[j + SEG_GROUP - 1];
-            const int knew = kz + skz;
-            const bool anew = active && (unsigned)knew < (unsigned)G.nz;
-            // the crossing after tzn, to detect two crossings inside one group
-            const float tz2 = (tzn < gend && anew)
-                                  ? tau_zplane(plane_at(knew + (skz > 0), G.dz, G.z0), inv_v, G.tc) : P_INF;
-            if (G.nz >= 2 && !__any_sync(0xffffffffu, tz2 < gend)) {
-                // voxel pair (kb, kb + 1) holding the lane's current slab kz and next slab knew
-                int kb = anew ? min(kz, knew) : (active ? (skz > 0 ? kz - 1 : kz) : 0);
-                kb = min(max(kb, 0), G.nz - 2);
-                const bool lo_old = kb == kz;
-                const float m_lo = ((lo_old && active) || (kb == knew && anew)) ? 1.0f : 0.0f;
-                const float m_hi = ((kb + 1 == kz && active) || (kb + 1 == knew && anew)) ? 1.0f : 0.0f;
-                // the lower voxel takes the part before the crossing if it is the current slab
-                const float sg = lo_old ? 1.0f : -1.0f, hg = lo_old ? 0.0f : 1.0f;
-                const float dt = fminf(tzn, 1e30f) - g0;
-                const float2 *base = pairs + kb * LINE_PITCH;
-                float acc_lo = 0.0f, acc_hi = 0.0f;
+            int knew[R];
+            bool anew[R];
+            float tz2[R];
+            bool dense = false;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                knew[r] = kz[r] + skz[r];
+                anew[r] = active[r] && (unsigned)knew[r] < (unsigned)G.nz;
+                // the crossing after tzn, to detect two crossings inside one group
+                tz2[r] = (tzn[r] < gend && anew[r])
+                             ? tau_zplane(plane_at(knew[r] + (skz[r] > 0), G.dz, G.z0), inv_v[r], G.tc) : P_INF;
+                dense = dense || tz2[r] < gend;
+            }
+            if (G.nz >= 2 && !__any_sync(0xffffffffu, dense)) {
+                // voxel pair (kb, kb + 1) holding a row's current slab kz and next slab knew
+                const float2 *base[R];
+                float m_lo[R], m_hi[R], sg[R], hg[R], dt[R], acc_lo[R], acc_hi[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    int kb = anew[r] ? min(kz[r], knew[r]) : (active[r] ? (skz[r] > 0 ? kz[r] - 1 : kz[r]) : 0);
+                    kb = min(max(kb, 0), G.nz - 2);
+                    const bool lo_old = kb == kz[r];
+                    m_lo[r] = ((lo_old && active[r]) || (kb == knew[r] && anew[r])) ? 1.0f : 0.0f;
+                    m_hi[r] = ((kb + 1 == kz[r] && active[r]) || (kb + 1 == knew[r] && anew[r])) ? 1.0f : 0.0f;
+                    // the lower voxel takes the part before the crossing if it is the current slab
+                    sg[r] = lo_old ? 1.0f : -1.0f;
+                    hg[r] = lo_old ? 0.0f : 1.0f;
+                    dt[r] = fminf(tzn[r], 1e30f) - g0;
+                    base[r] = pairs + kb * LINE_PITCH;
+                    acc_lo[r] = 0.0f;
+                    acc_hi[r] = 0.0f;
+                }
 #pragma unroll
                 for (int u = 0; u < SEG_GROUP; ++u) {
-                    const float4 sg4 = sSeg[j + u];
-                    const float flo = __saturatef(fmaf(sg, fmaf(dt, sg4.z, sg4.w), hg));
-                    const float wlo = sg4.y * flo, whi = sg4.y - wlo;
-                    const float2 v = base[u];
-                    acc_lo = fmaf(v.x, wlo, acc_lo);
-                    acc_hi = fmaf(v.y, whi, acc_hi);
+                    const float4 sg4 = sSeg[j + u]; // (column, length, 1/length, start term)
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float flo = __saturatef(fmaf(sg[r], fmaf(dt[r], sg4.z, sg4.w), hg[r]));
+                        const float wlo = sg4.y * flo, whi = sg4.y - wlo;
+                        const float2 v = base[r][u];
+                        acc_lo[r] = fmaf(v.x, wlo, acc_lo[r]);
+                        acc_hi[r] = fmaf(v.y, whi, acc_hi[r]);
+                    }
                 }
-                acc = fmaf(m_lo, acc_lo, fmaf(m_hi, acc_hi, acc));
-                if (tzn < gend) {
-                    kz = knew;
-                    active = anew;
-                    tzn = tz2;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    acc[r] = fmaf(m_lo[r], acc_lo[r], fmaf(m_hi[r], acc_hi[r], acc[r]));
+                    if (tzn[r] < gend) {
+                        kz[r] = knew[r];
+                        active[r] = anew[r];
+                        tzn[r] = tz2[r];
+                    }
                 }
             } else {
-                // a lane crosses several z planes in this group (or nz = 1): walk it exactly
+                // a row crosses several z planes in this group (or nz = 1): walk it exactly
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
 #pragma unroll 1
-                for (int u = 0; u < SEG_GROUP; ++u) {
-                    const float e = sEnd[j + u];
-                    float sl = u ? sEnd[j + u - 1] : g0;
-                    while (tzn < e) {
-                        if (active) acc = fmaf(kz < npair ? pairs[kz * LINE_PITCH + u].x : pairs[(kz - 1) * LINE_PITCH + u].y,
-                                               tzn - sl, acc);
-                        sl = tzn;
-                        kz += skz;
-                        active = (unsigned)kz < (unsigned)G.nz;
-                        tzn = active ? tau_zplane(plane_at(kz + (skz > 0), G.dz, G.z0), inv_v, G.tc) : P_INF;
+                    for (int u = 0; u < SEG_GROUP; ++u) {
+                        const float e = sEnd[j + u];
+                        float sl = u ? sEnd[j + u - 1] : g0;
+                        while (tzn[r] < e) {
+                            if (active[r])
+                                acc[r] = fmaf(kz[r] < npair ? pairs[kz[r] * LINE_PITCH + u].x
+                                                            : pairs[(kz[r] - 1) * LINE_PITCH + u].y,
+                                              tzn[r] - sl, acc[r]);
+                            sl = tzn[r];
+                            kz[r] += skz[r];
+                            active[r] = (unsigned)kz[r] < (unsigned)G.nz;
+                            tzn[r] = active[r] ? tau_zplane(plane_at(kz[r] + (skz[r] > 0), G.dz, G.z0), inv_v[r], G.tc)
+                                               : P_INF;
+                        }
+                        if (active[r])
+                            acc[r] = fmaf(kz[r] < npair ? pairs[kz[r] * LINE_PITCH + u].x
+                                                        : pairs[(kz[r] - 1) * LINE_PITCH + u].y,
+                                          e - sl, acc[r]);
                     }
-                    if (active) acc = fmaf(kz < npair ? pairs[kz * LINE_PITCH + u].x : pairs[(kz - 1) * LINE_PITCH + u].y,
-                                           e - sl, acc);
                 }
             }
             g0 = gend;
@@ -332,22 +374,23 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
 
     // ---- epilogue ----
     double red = 0.0;
-    if (row_ok) {
-        const size_t idx = ((size_t)view * G.nv + iv) * G.nu + iu;
-        const float q = acc * L;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (!ok[r]) continue;
+        const size_t idx = ((size_t)view * G.nv + iv[r]) * G.nu + iu;
+        const float q = acc[r] * L[r];
         if (MODE == PM_PLAIN) {
             out[idx] = q;
         } else if (MODE == PM_Q_PRESCALED) {
-            out[idx] = q * L;
-            red = (double)q * (double)q;
+            out[idx] = q * L[r];
+            red += (double)q * (double)q;
         } else if (MODE == PM_R_PRESCALED) {
-            const float r = y[idx] - q;
-            out[idx] = r * L;
-            red = (double)r * (double)r;
-        } else {
-            red = (double)cnt;
+            const float rr = y[idx] - q;
+            out[idx] = rr * L[r];
+            red += (double)rr * (double)rr;
         }
     }
+    if (MODE == PM_COUNT) red = (double)cnt;
     if (MODE != PM_PLAIN) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) red += __shfl_down_sync(0xffffffffu, red, o);
@@ -365,8 +408,8 @@ cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long 
                            long long sz, const float *y, float *out, int mode,
                            double *partials, float count_thr, cudaStream_t st)
 {
-    const int rows = proj_rows(G);
-    dim3 grid((unsigned)(G.nviews * G.nu), (unsigned)((G.nv + rows - 1) / rows));
+    const int rows = proj_threads(G); // threads per block; 2 rows each
+    dim3 grid((unsigned)(G.nviews * G.nu), (unsigned)((G.nv + 2 * rows - 1) / (2 * rows)));
     const size_t smem = project_smem(G);
     if (smem > 200 * 1024)
         return set_error(CBCT_ERR_UNSUPPORTED, "project: grid too large for the projector's shared memory (nx + ny and nz)");
