@@ -108,6 +108,27 @@ cbct_status cbct_backproject(const cbct_geometry *geom, const float *g, float *f
                              cbct_stream_t stream);
 
 /*
+ * The paper's own backprojector, Eq. (3) (Section 2.2.2, derived in Appendix 2): for every
+ * voxel centre x and view, the imager value at the point u* where the ray from the source
+ * through x meets the imager (bilinear interpolation, zero outside the imager), weighted
+ * by (dx dy dz / (du dv)) L^3(u*) / (L0 l^2(x)), summed over views. It approximates the
+ * exact adjoint (the paper reports the dot identity within about 1%); cbct_backproject
+ * computes the exact transpose instead. Same arguments and layouts as cbct_backproject.
+ */
+cbct_status cbct_backproject_eq3(const cbct_geometry *geom, const float *g, float *f,
+                                 cbct_stream_t stream);
+
+/*
+ * Batched P and exact P^T: `batch` volumes [batch][nz][ny][nx] and stacks
+ * [batch][n_views][nv][nu], contiguous, same geometry; item b is processed exactly as by
+ * cbct_project / cbct_backproject. batch = 0 does nothing.
+ */
+cbct_status cbct_project_batch(const cbct_geometry *geom, int batch, const float *f, float *g,
+                               cbct_stream_t stream);
+cbct_status cbct_backproject_batch(const cbct_geometry *geom, int batch, const float *g,
+                                   float *f, cbct_stream_t stream);
+
+/*
  * Tight-frame analysis alpha = W f (Section 2.1): alpha_i(x) = sum_k psi_i(k) f(x - k),
  * psi_i(k) = h_l(k_x) h_m(k_y) h_n(k_z) with h_0 = [1,2,1]/4, h_1 = sqrt(2)/4 [1,0,-1],
  * h_2 = [-1,2,-1]/4 (taps at offsets -1, 0, +1). The volume is periodic along every

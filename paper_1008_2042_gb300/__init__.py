@@ -56,6 +56,9 @@ _SIGNATURES = {
     "cbct_project": [_vp, _vp, _vp, _vp],
     "cbct_project_static": [_vp, _vp, _vp, _vp],
     "cbct_backproject": [_vp, _vp, _vp, _vp],
+    "cbct_backproject_eq3": [_vp, _vp, _vp, _vp],
+    "cbct_project_batch": [_vp, _i, _vp, _vp, _vp],
+    "cbct_backproject_batch": [_vp, _i, _vp, _vp, _vp],
     "cbct_tf_analyze": [_i, _i, _i, _vp, _vp, _vp],
     "cbct_tf_synthesize_shrink": [_i, _i, _i, _vp, _f, _i, _vp, _vp],
     "cbct_cgls": [_vp, _vp, _vp, _i, _vp],
@@ -207,6 +210,35 @@ def backproject(geom: Geometry, g: torch.Tensor, out: Optional[torch.Tensor] = N
         out = torch.empty(geom.vol_shape, dtype=torch.float32, device=g.device)
     _check(load_library().cbct_backproject(geom.handle, _dev(g, geom.proj_shape, "g"),
                                            _dev(out, geom.vol_shape, "out"), _stream(stream)))
+    return out
+
+
+def backproject_eq3(geom: Geometry, g: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """The paper's Eq. (3) backprojector (voxel-driven, bilinear): approximates P^T g."""
+    if out is None:
+        out = torch.empty(geom.vol_shape, dtype=torch.float32, device=g.device)
+    _check(load_library().cbct_backproject_eq3(geom.handle, _dev(g, geom.proj_shape, "g"),
+                                               _dev(out, geom.vol_shape, "out"), _stream(stream)))
+    return out
+
+
+def project_batch(geom: Geometry, f: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """P of a batch of volumes (B, nz, ny, nx) -> (B, n_views, nv, nu)."""
+    b = f.shape[0]
+    if out is None:
+        out = torch.empty((b,) + geom.proj_shape, dtype=torch.float32, device=f.device)
+    _check(load_library().cbct_project_batch(geom.handle, int(b), _dev(f, (b,) + geom.vol_shape, "f"),
+                                             _dev(out, (b,) + geom.proj_shape, "out"), _stream(stream)))
+    return out
+
+
+def backproject_batch(geom: Geometry, g: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Exact P^T of a batch of stacks (B, n_views, nv, nu) -> (B, nz, ny, nx)."""
+    b = g.shape[0]
+    if out is None:
+        out = torch.empty((b,) + geom.vol_shape, dtype=torch.float32, device=g.device)
+    _check(load_library().cbct_backproject_batch(geom.handle, int(b), _dev(g, (b,) + geom.proj_shape, "g"),
+                                                 _dev(out, (b,) + geom.vol_shape, "out"), _stream(stream)))
     return out
 
 

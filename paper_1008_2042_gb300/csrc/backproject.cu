@@ -295,4 +295,56 @@ cbct_status launch_row_prefix(const GeomDev &G, const float *g, float2 *ps, int 
     return check_cuda(cudaGetLastError(), "row prefix launch");
 }
 
+
+// The paper's own backprojector, Eq. (3): voxel-driven, for every view the imager value at
+// the point u* where the ray through the voxel centre x meets the imager is taken by
+// bilinear interpolation (zero outside the imager) and weighted by
+// (dx dy dz / (du dv)) L^3(u*) / (L0 l^2(x)) with L0 = sdd, l = |x - S|, L = |u* - S|.
+// With w the distance of x from the source along the central ray, L = l sdd / w, so the
+// weight is (dx dy dz / (du dv)) l sdd^2 / w^3. It approximates the exact adjoint
+// (Appendix 2). Thread per voxel, lanes along x (public x-fastest layout).
+__global__ void __launch_bounds__(128)
+k_backproject_eq3(GeomDev G, const float *__restrict__ g, float *__restrict__ f, float pref)
+{
+    const int ix = blockIdx.x * 32 + threadIdx.x, iy = blockIdx.y * 4 + threadIdx.y, iz = blockIdx.z;
+    if (ix >= G.nx || iy >= G.ny) return;
+    const float px = fmaf((float)ix + 0.5f, G.dx, G.x0);
+    const float py = fmaf((float)iy + 0.5f, G.dy, G.y0);
+    const float pz = fmaf((float)iz + 0.5f, G.dz, G.z0);
+    const float sdd2 = G.sdd * G.sdd;
+    float acc = 0.0f;
+    for (int k = 0; k < G.nviews; ++k) {
+        const float2 cs = G.cs[k];
+        const float w = G.sad - fmaf(px, cs.x, py * cs.y);
+        const float inv_w = 1.0f / w;
+        const float u = G.sdd * fmaf(-px, cs.y, py * cs.x) * inv_w;
+        const float v = G.sdd * pz * inv_w;
+        const float fu = (u - G.u_first) * G.inv_du, fv = (v - G.v_first) * G.inv_dv;
+        const float flu = floorf(fu), flv = floorf(fv);
+        const int i0 = (int)flu, j0 = (int)flv;
+        const float wu = fu - flu, wv = fv - flv;
+        const float *gk = g + (size_t)k * G.nv * G.nu;
+        float val = 0.0f;
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const int iu = i0 + a, iv = j0 + b;
+                if (iu >= 0 && iu < G.nu && iv >= 0 && iv < G.nv)
+                    val = fmaf((a ? wu : 1.0f - wu) * (b ? wv : 1.0f - wv), __ldg(gk + (size_t)iv * G.nu + iu), val);
+            }
+        const float dxs = fmaf(-G.sad, cs.x, px), dys = fmaf(-G.sad, cs.y, py);
+        const float l = sqrtf(fmaf(dxs, dxs, fmaf(dys, dys, pz * pz)));
+        acc = fmaf(pref * l * sdd2 * inv_w * inv_w * inv_w, val, acc);
+    }
+    f[((size_t)iz * G.ny + iy) * G.nx + ix] = acc;
+}
+
+cbct_status launch_backproject_eq3(const GeomDev &G, const float *g, float *f, float pref, cudaStream_t st)
+{
+    dim3 grid((G.nx + 31) / 32, (G.ny + 3) / 4, G.nz), block(32, 4);
+    CBCT_TIMED(CBCT_KERNEL_BACKPROJECT, st, k_backproject_eq3<<<grid, block, 0, st>>>(G, g, f, pref));
+    return check_cuda(cudaGetLastError(), "backproject_eq3 launch");
+}
+
 } // namespace cbct

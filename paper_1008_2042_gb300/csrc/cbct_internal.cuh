@@ -141,6 +141,8 @@ cbct_status launch_backproject(const GeomDev &G, const float2 *ps, float *out, l
                                cudaStream_t st);
 cbct_status launch_row_prefix(const GeomDev &G, const float *g, float2 *ps, int prescale,
                               cudaStream_t st);
+cbct_status launch_backproject_eq3(const GeomDev &G, const float *g, float *f, float pref,
+                                   cudaStream_t st);
 
 cbct_status launch_tf_analyze(int n0, int n1, int n2, const float *f, float *alpha,
                               cudaStream_t st);

@@ -618,3 +618,35 @@ extern "C" cbct_status cbct_restrict(int nx, int ny, int nz, double dx, double d
                                                                 cdx, cdy, cdz, 0));
     return check_cuda(cudaGetLastError(), "restrict launch");
 }
+
+extern "C" cbct_status cbct_backproject_eq3(const cbct_geometry *gc, const float *gin, float *f, cbct_stream_t stream)
+{
+    TRY(check_geom(gc, "backproject_eq3"));
+    if (!gin || !f) return set_error(CBCT_ERR_INVALID_ARG, "backproject_eq3: null pointer");
+    const GeomDev G = level_geom(gc, 0);
+    const cbct_geometry_desc &d = gc->desc;
+    const float pref = (float)(d.dx * d.dy * d.dz / (d.du * d.dv));
+    return launch_backproject_eq3(G, gin, f, pref, (cudaStream_t)stream);
+}
+
+extern "C" cbct_status cbct_project_batch(const cbct_geometry *gc, int batch, const float *f, float *g,
+                                          cbct_stream_t stream)
+{
+    TRY(check_geom(gc, "project_batch"));
+    if (batch < 0 || (batch > 0 && (!f || !g))) return set_error(CBCT_ERR_INVALID_ARG, "project_batch: bad arguments");
+    const cbct_geometry_desc &d = gc->desc;
+    const size_t N = (size_t)d.nx * d.ny * d.nz, M = (size_t)d.n_views * d.nv * d.nu;
+    for (int b = 0; b < batch; ++b) TRY(cbct_project(gc, f + b * N, g + b * M, stream));
+    return CBCT_OK;
+}
+
+extern "C" cbct_status cbct_backproject_batch(const cbct_geometry *gc, int batch, const float *g, float *f,
+                                              cbct_stream_t stream)
+{
+    TRY(check_geom(gc, "backproject_batch"));
+    if (batch < 0 || (batch > 0 && (!f || !g))) return set_error(CBCT_ERR_INVALID_ARG, "backproject_batch: bad arguments");
+    const cbct_geometry_desc &d = gc->desc;
+    const size_t N = (size_t)d.nx * d.ny * d.nz, M = (size_t)d.n_views * d.nv * d.nu;
+    for (int b = 0; b < batch; ++b) TRY(cbct_backproject(gc, g + b * M, f + b * N, stream));
+    return CBCT_OK;
+}

@@ -163,3 +163,26 @@ def test_restrict_parity(cb):
     out = cb.restrict(dev(ff), (1.0, 1.0, 2.0), (9, 16, 12), (2.0, 2.0, 4.0)).cpu().numpy()
     ref = oracle.restrict(ff, (1.0, 1.0, 2.0), (9, 16, 12), (2.0, 2.0, 4.0))
     assert rel(out, ref) <= 1e-6, rel(out, ref)
+
+
+@pytest.mark.parametrize("name", ["small", "odd", "tall"])
+def test_backproject_eq3_parity(cb, name):
+    """The paper's own backprojector, Eq. (3), against the oracle's restatement."""
+    geom = GEOMS[name]
+    y = synth.random_projections(geom, 105)
+    with cb.Geometry(geom) as g:
+        b = cb.backproject_eq3(g, dev(y)).cpu().numpy()
+    ref = oracle.backproject_eq3(geom, y)
+    assert rel(b, ref) <= 1e-4, rel(b, ref)
+
+
+def test_batched_operators_equal_single_calls(cb):
+    geom = GEOMS["odd"]
+    fs = np.stack([synth.random_volume(geom, 200 + b) for b in range(3)])
+    ys = np.stack([synth.random_projections(geom, 300 + b) for b in range(3)])
+    with cb.Geometry(geom) as g:
+        pb = cb.project_batch(g, dev(fs)).cpu().numpy()
+        bb = cb.backproject_batch(g, dev(ys)).cpu().numpy()
+        for b in range(3):
+            assert np.array_equal(pb[b], cb.project(g, dev(fs[b])).cpu().numpy())
+            assert np.array_equal(bb[b], cb.backproject(g, dev(ys[b])).cpu().numpy())
