@@ -150,6 +150,15 @@ cbct_status cbct_tf_synthesize_shrink(int nx, int ny, int nz, const float *alpha
                                       cbct_stream_t stream);
 
 /*
+ * The regularisation step of Algorithms A1/A2 in one pass: f_out = H(W^T T_mu W f)
+ * (Section 2.1, Eq. (2)), equal to cbct_tf_analyze followed by cbct_tf_synthesize_shrink
+ * but without materialising the 27 coefficient channels (they stay on chip). Periodic
+ * boundary, layouts as above. f and f_out must not overlap.
+ */
+cbct_status cbct_tf_shrink(int nx, int ny, int nz, const float *f, float mu, int positivity,
+                           float *f_out, cbct_stream_t stream);
+
+/*
  * CGLS (Appendix 1): n_iter updates of x for min ||P x - y||^2 starting from x.
  * Inner products are accumulated in FP64 on the device; if ||P^T r||^2 or ||P p||^2
  * becomes zero the remaining updates leave x unchanged.

@@ -61,6 +61,7 @@ _SIGNATURES = {
     "cbct_backproject_batch": [_vp, _i, _vp, _vp, _vp],
     "cbct_tf_analyze": [_i, _i, _i, _vp, _vp, _vp],
     "cbct_tf_synthesize_shrink": [_i, _i, _i, _vp, _f, _i, _vp, _vp],
+    "cbct_tf_shrink": [_i, _i, _i, _vp, _f, _i, _vp, _vp],
     "cbct_cgls": [_vp, _vp, _vp, _i, _vp],
     "cbct_reconstruct": [_vp, _vp, _f, _f, _i, ctypes.POINTER(_i), _vp, _vp],
     "cbct_reconstruct_ex": [_vp, _vp, _f, _f, _i, ctypes.POINTER(_i), ctypes.POINTER(ReconOpts),
@@ -261,6 +262,17 @@ def tf_synthesize_shrink(alpha: torch.Tensor, mu: float, positivity: bool = True
     _check(load_library().cbct_tf_synthesize_shrink(nx, ny, nz, _dev(alpha, None, "alpha"), float(mu),
                                                     int(bool(positivity)), _dev(out, (nz, ny, nx), "out"),
                                                     _stream(stream)))
+    return out
+
+
+def tf_shrink(f: torch.Tensor, mu: float, positivity: bool = True, out: Optional[torch.Tensor] = None,
+              stream=None) -> torch.Tensor:
+    """f_out = H(W^T T_mu W f) in one fused pass (coefficients never stored)."""
+    nz, ny, nx = f.shape
+    if out is None:
+        out = torch.empty((nz, ny, nx), dtype=torch.float32, device=f.device)
+    _check(load_library().cbct_tf_shrink(nx, ny, nz, _dev(f, None, "f"), float(mu), int(bool(positivity)),
+                                         _dev(out, (nz, ny, nx), "out"), _stream(stream)))
     return out
 
 

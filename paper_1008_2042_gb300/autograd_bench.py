@@ -36,7 +36,8 @@ def main(argv=None):
     geom = synth.Geometry(nx=256, ny=256, nz=64, dx=1.0, dy=1.0, dz=1.0, nu=256, nv=192, du=1.5, dv=1.5,
                           n_views=60)
     g = cb.Geometry(geom)
-    fs = [synth.voxelize(geom, synth.random_ellipsoids(geom, 1004 + b, n=8)) for b in range(a.batch)]
+    import numpy as np
+    fs = np.stack([synth.voxelize(geom, synth.random_ellipsoids(geom, 1004 + b, n=8)) for b in range(a.batch)])
     f = torch.tensor(fs, dtype=torch.float32, device="cuda")
     y = torch.rand((a.batch,) + geom.proj_shape, device="cuda") * 3.0
     nnz = cb.count_nnz(g)

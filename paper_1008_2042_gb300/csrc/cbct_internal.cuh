@@ -148,6 +148,10 @@ cbct_status launch_tf_analyze(int n0, int n1, int n2, const float *f, float *alp
                               cudaStream_t st);
 cbct_status launch_tf_synth_shrink(int n0, int n1, int n2, const float *alpha, float mu,
                                    int positivity, float *f, cudaStream_t st);
+// Fused f_new = H(W^T T_mu W x) and, if vout != nullptr, v = f_new + coef (f_new - f_old).
+cbct_status launch_tf_shrink_fused(int n0, int n1, int n2, const float *x, float mu, int positivity,
+                                   float *fnew, const float *fold, float coef, float *vout,
+                                   cudaStream_t st);
 // Public x-fastest [nz][ny][nx] <-> internal z-fastest [ny][nx][nz] volume layout.
 cbct_status transpose(const float *in, float *out, int nx, int ny, int nz, bool to_internal,
                       cudaStream_t st);

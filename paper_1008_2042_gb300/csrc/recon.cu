@@ -115,16 +115,6 @@ __global__ void k_update_xp(float *__restrict__ x, float *__restrict__ p, const 
     }
 }
 
-// A2 step 1: v = f_new + c (f_new - f_old)
-__global__ void k_momentum(float *__restrict__ v, const float *__restrict__ fn, const float *__restrict__ fo,
-                           float c, size_t n)
-{
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const float a = fn[i];
-        v[i] = fmaf(c, a - fo[i], a);
-    }
-}
-
 // ------------------------------------------------------------------------------------
 // Layout conversion: public x-fastest [z][y][x] <-> internal z-fastest [y][x][z]
 // ------------------------------------------------------------------------------------
@@ -288,7 +278,7 @@ static cbct_status launch_prolong(const Grid3 &cg, const float *fc, const Grid3 
 // ------------------------------------------------------------------------------------
 
 struct Work {
-    float *X, *P, *S, *Fa, *Fb, *R, *Q, *alpha;
+    float *X, *X2, *P, *S, *Fa, *Fb, *R, *Q; // X, X2: the CGLS iterate and the next momentum point
     float2 *PS; // row prefix sums of the prescaled residual, input of the adjoint
     double *partials;
     Scalars *sc;
@@ -317,14 +307,13 @@ static size_t work_layout(const cbct_geometry *g, char *base, Work *w)
         off += align256(bytes);
         return p;
     };
-    float *X = (float *)take(4 * N), *P = (float *)take(4 * N), *S = (float *)take(4 * N);
+    float *X = (float *)take(4 * N), *X2 = (float *)take(4 * N), *P = (float *)take(4 * N), *S = (float *)take(4 * N);
     float *Fa = (float *)take(4 * N), *Fb = (float *)take(4 * N);
     float *R = (float *)take(4 * M), *Q = (float *)take(4 * M);
-    float *alpha = (float *)take(4 * 27 * N);
     float2 *PS = (float2 *)take(sizeof(float2) * prefix_elems(d));
     double *partials = (double *)take(sizeof(double) * max_partials(g));
     Scalars *sc = (Scalars *)take(sizeof(Scalars));
-    if (w) *w = Work{X, P, S, Fa, Fb, R, Q, alpha, PS, partials, sc};
+    if (w) *w = Work{X, X2, P, S, Fa, Fb, R, Q, PS, partials, sc};
     return off;
 }
 
@@ -417,7 +406,7 @@ static cbct_status reset_scalars(const Work &w, cudaStream_t st)
 // ------------------------------------------------------------------------------------
 
 static cbct_status run_a2(const GeomDev &G, const float *y, float mu, int iters, const cbct_recon_opts &o,
-                          const Work &w, float **f_cur, float **f_other, cudaStream_t st)
+                          Work &w, float **f_cur, float **f_other, cudaStream_t st)
 {
     const size_t N = (size_t)G.nx * G.ny * G.nz;
     // v^(0) = f^(0): the first momentum coefficient is 0
@@ -425,19 +414,20 @@ static cbct_status run_a2(const GeomDev &G, const float *y, float mu, int iters,
     double t = 1.0; // t^(k)
     for (int k = 0; k < iters; ++k) {
         TRY(run_cgls(G, y, w.X, o.n_cgls, w, st));
-        // f^(k+1) = H(D^T T_mu D x); internal layout: axis 0 = z, axis 1 = x, axis 2 = y
-        TRY(launch_tf_analyze(G.nz, G.nx, G.ny, w.X, w.alpha, st));
-        TRY(launch_tf_synth_shrink(G.nz, G.nx, G.ny, w.alpha, mu, o.positivity, *f_other, st));
+        // f^(k+1) = H(D^T T_mu D x) fused with the next momentum point
+        // v^(k+1) = f^(k+1) + (t^(k) - 1) / t^(k+1) (f^(k+1) - f^(k)) into X2;
+        // internal layout: axis 0 = z, axis 1 = x, axis 2 = y
         const double t_next = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
-        if (k + 1 < iters) {
-            // v^(k+1) = f^(k+1) + (t^(k) - 1) / t^(k+1) (f^(k+1) - f^(k))
-            const float c = o.momentum ? (float)((t - 1.0) / t_next) : 0.0f;
-            CBCT_TIMED(CBCT_KERNEL_OTHER, st, k_momentum<<<vec_blocks(N), 256, 0, st>>>(w.X, *f_other, *f_cur, c, N));
-            TRY(check_cuda(cudaGetLastError(), "momentum launch"));
-        }
+        const bool last = k + 1 == iters;
+        const float c = o.momentum ? (float)((t - 1.0) / t_next) : 0.0f;
+        TRY(launch_tf_shrink_fused(G.nz, G.nx, G.ny, w.X, mu, o.positivity, *f_other, *f_cur, c,
+                                   last ? nullptr : w.X2, st));
         float *tmp = *f_cur;
         *f_cur = *f_other;
         *f_other = tmp;
+        tmp = w.X;
+        w.X = w.X2;
+        w.X2 = tmp;
         t = t_next;
     }
     return CBCT_OK;
@@ -649,4 +639,15 @@ extern "C" cbct_status cbct_backproject_batch(const cbct_geometry *gc, int batch
     const size_t N = (size_t)d.nx * d.ny * d.nz, M = (size_t)d.n_views * d.nv * d.nu;
     for (int b = 0; b < batch; ++b) TRY(cbct_backproject(gc, g + b * M, f + b * N, stream));
     return CBCT_OK;
+}
+
+extern "C" cbct_status cbct_tf_shrink(int nx, int ny, int nz, const float *f, float mu, int positivity, float *out,
+                                      cbct_stream_t stream)
+{
+    if (nx < 1 || ny < 1 || nz < 1) return set_error(CBCT_ERR_INVALID_ARG, "tf_shrink: sizes must be >= 1");
+    if (ny > 65535 * 8) return set_error(CBCT_ERR_INVALID_ARG, "tf_shrink: ny too large");
+    if (!f || !out) return set_error(CBCT_ERR_INVALID_ARG, "tf_shrink: null pointer");
+    if (f == out) return set_error(CBCT_ERR_INVALID_ARG, "tf_shrink: input and output must differ");
+    if (!(mu >= 0.0f) || !std::isfinite(mu)) return set_error(CBCT_ERR_INVALID_ARG, "tf_shrink: mu must be finite and >= 0");
+    return launch_tf_shrink_fused(nx, ny, nz, f, mu, positivity, out, nullptr, 0.0f, nullptr, (cudaStream_t)stream);
 }

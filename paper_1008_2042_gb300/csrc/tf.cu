@@ -240,3 +240,155 @@ cbct_status launch_tf_synth_shrink(int n0, int n1, int n2, const float *alpha, f
 }
 
 } // namespace cbct
+
+namespace cbct {
+
+// ------------------------------------------------------------------------------------
+// Fused shrinkage step of Algorithm A2 (steps 3-4, then step 1 of the next iteration):
+//   f_new = H(W^T T_mu W x)   and optionally   v = f_new + c (f_new - f_old).
+// A block owns a TA x TB tile of the (axis 0, axis 1) plane and marches along axis 2. For
+// every plane c' it computes the 27 coefficients on the tile plus a one-voxel halo from a
+// ring of three x planes (tile plus a two-voxel halo) in shared memory, shrinks them
+// (Eq. (2)), synthesises along axis 0 and axis 1 in shared memory, and keeps the three
+// axis-2 partial sums of the last three planes in registers to finish plane c' - 1.
+// The coefficients never leave the SM: HBM traffic is one read of x (plus halo re-reads
+// that hit L2) and the writes of f_new (and v, with one read of f_old).
+// ------------------------------------------------------------------------------------
+constexpr int FX_A = TA + 4, FX_B = TB + 4;  // x tile with a two-voxel halo
+constexpr int FA_A = TA + 2, FA_B = TB + 2;  // coefficient tile with a one-voxel halo
+constexpr int FX_PLANE = FX_A * FX_B;
+constexpr int FA_PLANE = FA_A * FA_B;
+constexpr int FU_PLANE = FA_B * TA;
+constexpr size_t TF_FUSED_SMEM = sizeof(float) * (3 * FX_PLANE + 27 * FA_PLANE + 9 * FU_PLANE);
+
+__global__ void __launch_bounds__(TF_THREADS)
+k_tf_shrink_fused(int n0, int n1, int n2, int chunk, const float *__restrict__ x, float mu, int positivity,
+                  float *__restrict__ fnew, const float *__restrict__ fold, float coef, float *__restrict__ vout)
+{
+    extern __shared__ float sm[];
+    float *sx = sm;                         // [3][FX_B][FX_A] ring of x planes
+    float *sa = sx + 3 * FX_PLANE;          // [27][FA_B][FA_A] shrunk coefficients of plane c'
+    float *su = sa + 27 * FA_PLANE;         // [9][FA_B][TA] after synthesis along axis 0
+    const int a0 = blockIdx.x * TA, b0 = blockIdx.y * TB;
+    const int c_begin = blockIdx.z * chunk;
+    const int c_end = min(n2, c_begin + chunk);
+    if (c_begin >= c_end) return;
+    const int tid = threadIdx.y * TA + threadIdx.x;
+    const int ta = threadIdx.x, tb = threadIdx.y;
+    const bool inside = a0 + ta < n0 && b0 + tb < n1;
+
+    // in-plane source offsets of the (at most two) x-tile positions this thread loads
+    int off[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int pos = tid + k * TF_THREADS;
+        if (pos < FX_PLANE) {
+            const int r = pos / FX_A, q = pos - r * FX_A;
+            off[k] = wrapi(b0 + r - 2, n1) * n0 + wrapi(a0 + q - 2, n0);
+        } else {
+            off[k] = -1;
+        }
+    }
+    auto load_x = [&](int c, int slot) {
+        const float *src = x + (size_t)wrapi(c, n2) * n1 * n0;
+        float *d = sx + slot * FX_PLANE;
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            if (off[k] >= 0) d[tid + k * TF_THREADS] = __ldg(src + off[k]);
+    };
+
+    // planes c' run from c_begin - 1 to c_end; the ring holds x(c'-1), x(c'), x(c'+1)
+    load_x(c_begin - 2, 0);
+    load_x(c_begin - 1, 1);
+    float w_m2[3] = {0.f, 0.f, 0.f}, w_m1[3] = {0.f, 0.f, 0.f}; // w_n at planes c'-2, c'-1
+    for (int s = 0; s <= c_end - c_begin + 1; ++s) {
+        const int cp = c_begin - 1 + s;
+        load_x(cp + 1, (s + 2) % 3);
+        __syncthreads();
+        const float *xm = sx + (s % 3) * FX_PLANE, *x0 = sx + ((s + 1) % 3) * FX_PLANE,
+                    *xp = sx + ((s + 2) % 3) * FX_PLANE; // planes cp-1, cp, cp+1
+        // 1. coefficients of plane cp on the tile + halo, shrunk (Eq. (2))
+        for (int pos = tid; pos < FA_PLANE; pos += TF_THREADS) {
+            const int r = pos / FA_A, q = pos - r * FA_A; // x-tile position (r + 1, q + 1)
+            float u3[3][3][3];                             // [cc][m][l]
+            const float *pl[3] = {xm, x0, xp};
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                float t[3][3];
+#pragma unroll
+                for (int bb = 0; bb < 3; ++bb) {
+                    const float *row = pl[cc] + (r + bb) * FX_A + q;
+                    ana3(row[0], row[1], row[2], t[bb][0], t[bb][1], t[bb][2]);
+                }
+#pragma unroll
+                for (int l = 0; l < 3; ++l) ana3(t[0][l], t[1][l], t[2][l], u3[cc][0][l], u3[cc][1][l], u3[cc][2][l]);
+            }
+            float al[27];
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+                for (int l = 0; l < 3; ++l)
+                    ana3(u3[0][m][l], u3[1][m][l], u3[2][m][l], al[l + 3 * m], al[l + 3 * m + 9], al[l + 3 * m + 18]);
+            float s2 = 0.0f;
+#pragma unroll
+            for (int ch = 1; ch < 27; ++ch) s2 = fmaf(al[ch], al[ch], s2);
+            const float nrm = sqrtf(s2);
+            const float scale = nrm > mu ? 1.0f - mu / nrm : 0.0f;
+            sa[pos] = al[0];
+#pragma unroll
+            for (int ch = 1; ch < 27; ++ch) sa[ch * FA_PLANE + pos] = al[ch] * scale;
+        }
+        __syncthreads();
+        // 2. synthesis along axis 0: u_{mn} = sum_l, for TA x (TB+2) positions
+        for (int i = tid; i < 9 * FU_PLANE; i += TF_THREADS) {
+            const int mn = i / FU_PLANE, rem = i - mn * FU_PLANE;
+            const int r = rem / TA, q = rem - r * TA;
+            const float *b0p = sa + (3 * mn) * FA_PLANE + r * FA_A + q; // l = 0
+            const float *b1p = b0p + FA_PLANE, *b2p = b1p + FA_PLANE;
+            su[i] = syn3(b0p[0], b0p[1], b0p[2], b1p[0], b1p[2], b2p[0], b2p[1], b2p[2]);
+        }
+        __syncthreads();
+        // 3. synthesis along axis 1: w_n = sum_m
+        float w[3];
+#pragma unroll
+        for (int n = 0; n < 3; ++n) {
+            const float *m0 = su + (3 * n + 0) * FU_PLANE + tb * TA + ta;
+            const float *m1 = m0 + FU_PLANE, *m2 = m1 + FU_PLANE;
+            w[n] = syn3(m0[0], m0[TA], m0[2 * TA], m1[0], m1[2 * TA], m2[0], m2[TA], m2[2 * TA]);
+        }
+        // 4. synthesis along axis 2 gives plane cp - 1; positivity; momentum point
+        if (s >= 2 && inside) {
+            float o = syn3(w_m2[0], w_m1[0], w[0], w_m2[1], w[1], w_m2[2], w_m1[2], w[2]);
+            if (positivity && o < 0.0f) o = 0.0f;
+            const size_t idx = ((size_t)(cp - 1) * n1 + (b0 + tb)) * n0 + (a0 + ta);
+            fnew[idx] = o;
+            if (vout) vout[idx] = fmaf(coef, o - __ldg(fold + idx), o);
+        }
+#pragma unroll
+        for (int n = 0; n < 3; ++n) {
+            w_m2[n] = w_m1[n];
+            w_m1[n] = w[n];
+        }
+        __syncthreads();
+    }
+}
+
+cbct_status launch_tf_shrink_fused(int n0, int n1, int n2, const float *x, float mu, int positivity, float *fnew,
+                                   const float *fold, float coef, float *vout, cudaStream_t st)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_tf_shrink_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)TF_FUSED_SMEM);
+        if (e != cudaSuccess) return check_cuda(e, "tf_shrink_fused attribute");
+        attr_set = true;
+    }
+    const int chunk = tf_chunk(n0, n1, n2);
+    dim3 grid((n0 + TA - 1) / TA, (n1 + TB - 1) / TB, (n2 + chunk - 1) / chunk);
+    CBCT_TIMED(CBCT_KERNEL_TF_SYNTH, st,
+               k_tf_shrink_fused<<<grid, dim3(TA, TB), TF_FUSED_SMEM, st>>>(n0, n1, n2, chunk, x, mu, positivity,
+                                                                            fnew, fold, coef, vout));
+    return check_cuda(cudaGetLastError(), "tf_shrink_fused launch");
+}
+
+} // namespace cbct

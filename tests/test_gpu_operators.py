@@ -139,6 +139,17 @@ def test_tf_synthesize_shrink_parity(cb, shape, positive):
     assert rel(out, ref) <= 1e-5, rel(out, ref)
 
 
+@pytest.mark.parametrize("shape", TF_SHAPES)
+@pytest.mark.parametrize("positive", [False, True])
+def test_tf_shrink_fused_parity(cb, shape, positive):
+    """The fused regularisation step H(W^T T_mu W f) against the oracle's three steps."""
+    f = np.random.default_rng(10).standard_normal(shape)
+    mu = float(np.median(np.sqrt((oracle.tf_analyze(f)[1:] ** 2).sum(0))))
+    out = cb.tf_shrink(dev(f), mu, positive).cpu().numpy()
+    ref = oracle.tf_synthesize_shrink(oracle.tf_analyze(f), mu, positive)
+    assert rel(out, ref) <= 1e-5, rel(out, ref)
+
+
 def test_tf_round_trip_identity(cb):
     f = np.random.default_rng(7).standard_normal((16, 64, 64))
     ft = dev(f)
