@@ -146,8 +146,12 @@ def test_tf_shrink_fused_parity(cb, shape, positive):
     f = np.random.default_rng(10).standard_normal(shape)
     mu = float(np.median(np.sqrt((oracle.tf_analyze(f)[1:] ** 2).sum(0))))
     out = cb.tf_shrink(dev(f), mu, positive).cpu().numpy()
-    ref = oracle.tf_synthesize_shrink(oracle.tf_analyze(f), mu, positive)
-    assert rel(out, ref) <= 1e-5, rel(out, ref)
+    alpha = oracle.tf_analyze(f)
+    ref = oracle.tf_synthesize_shrink(alpha, mu, positive)
+    # H is a projection (1-Lipschitz): measure against the output's size before H, which
+    # stays meaningful when H zeroes most voxels of a tiny random volume
+    scale = np.linalg.norm(oracle.tf_synthesize_shrink(alpha, mu, False))
+    assert np.linalg.norm(out - ref) <= 1e-5 * scale, np.linalg.norm(out - ref) / scale
 
 
 def test_tf_round_trip_identity(cb):
