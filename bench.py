@@ -59,6 +59,8 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--views", type=int, default=40, choices=(40, 80))
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--storage", default="f32", choices=("f32", "bf16", "f16"),
+                    help="storage type of the CGLS residual and projected direction (arithmetic stays FP32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-views", type=int, default=40,
                     help="views in the oracle's bounded sample (CPU baseline); the reference arm uses 16 per step")
@@ -301,7 +303,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step(y_in, o):
-        cb.reconstruct(g, y_in, MU, LEVELS, iters, n_cgls=N_CGLS, workspace=ws, out=o)
+        cb.reconstruct(g, y_in, MU, LEVELS, iters, n_cgls=N_CGLS, workspace=ws, out=o, storage=args.storage)
 
     for _ in range(max(args.warmup, 0)):
         step(y, out)
@@ -399,6 +401,7 @@ def run_ours(args):
             "config": workload_config(geom, iters, {"nnz_per_P": nnz,
                                                     "updates_per_step": updates,
                                                     "recon_seconds": secs / args.steps,
+                                                    "cgls_vector_storage": args.storage,
                                                     "parallelism": f"replicas x{world}"}),
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(y_host.numel() * 4),

@@ -64,6 +64,19 @@ typedef struct {
     const double *angles;    /* host array of n_views angles (rad); NULL = 2 pi k / n_views */
 } cbct_geometry_desc;
 
+/*
+ * Storage type of projections and frame coefficients in the typed (_ex) entry points and
+ * of the projection-domain vectors inside CGLS. Arithmetic is FP32 whatever the storage
+ * (line integrals, stencils, updates), inner products and norms FP64. The paper computes
+ * in FP32 throughout; the 16-bit storage types have no counterpart there.
+ * BF16 and FP16 values are IEEE-style binary16 / bfloat16, round-to-nearest-even.
+ */
+typedef enum {
+    CBCT_F32 = 0,  /* float */
+    CBCT_BF16 = 1, /* bfloat16: 8 significand bits, FP32's exponent range */
+    CBCT_F16 = 2   /* IEEE binary16: 11 significand bits, |x| < 65504 */
+} cbct_dtype;
+
 /* Opaque, library-owned geometry: per-view tables and device scratch. */
 typedef struct cbct_geometry cbct_geometry;
 
@@ -72,6 +85,9 @@ typedef struct {
     int n_cgls;     /* CGLS updates per outer iteration (Appendix 1: "M = 2~3"); default 3 */
     int momentum;   /* 1 = Algorithm A2 (default), 0 = Algorithm A1 */
     int positivity; /* 1 = apply H after the shrinkage (default), 0 = skip H */
+    int storage;    /* cbct_dtype of the CGLS residual r and projected direction q (default
+                       CBCT_F32). With CBCT_F16, q is stored as q / ||P^T r|| so that it stays
+                       in range; y, x, p, s and f stay FP32. */
 } cbct_recon_opts;
 
 /*
@@ -96,6 +112,14 @@ cbct_status cbct_project(const cbct_geometry *geom, const float *f, float *g,
                          cbct_stream_t stream);
 
 /*
+ * cbct_project with the projections stored as g_type (FP32 arithmetic, one rounding of
+ * every line integral to the storage type). g: device [n_views][nv][nu] of g_type.
+ * Errors: as cbct_project; INVALID_ARG for an unknown g_type.
+ */
+cbct_status cbct_project_ex(const cbct_geometry *geom, const float *f, void *g,
+                            cbct_dtype g_type, cbct_stream_t stream);
+
+/*
  * Exact adjoint f = P^T g: f_j = sum_i a_ij g_i with the same a_ij as cbct_project, so
  * <P f, g> = <f, P^T g> (Eq. (A1)). Computed by gathering per voxel (no atomics; the
  * result does not depend on scheduling). The paper's own backprojector (Eq. (3)) is an
@@ -106,6 +130,10 @@ cbct_status cbct_project(const cbct_geometry *geom, const float *f, float *g,
  */
 cbct_status cbct_backproject(const cbct_geometry *geom, const float *g, float *f,
                              cbct_stream_t stream);
+
+/* cbct_backproject reading projections stored as g_type (widened to FP32 on load). */
+cbct_status cbct_backproject_ex(const cbct_geometry *geom, const void *g, cbct_dtype g_type,
+                                float *f, cbct_stream_t stream);
 
 /*
  * The paper's own backprojector, Eq. (3) (Section 2.2.2, derived in Appendix 2): for every
@@ -138,6 +166,10 @@ cbct_status cbct_backproject_batch(const cbct_geometry *geom, int batch, const f
 cbct_status cbct_tf_analyze(int nx, int ny, int nz, const float *f, float *alpha27,
                             cbct_stream_t stream);
 
+/* cbct_tf_analyze storing the 27 channels as a_type (FP32 stencils, one rounding each). */
+cbct_status cbct_tf_analyze_ex(int nx, int ny, int nz, const float *f, void *alpha27,
+                               cbct_dtype a_type, cbct_stream_t stream);
+
 /*
  * Shrinkage and synthesis f = H(W^T T_mu alpha) (Eq. (2) and Section 2.1): at every
  * voxel the 26 high-pass coefficients are scaled by max(1 - mu / ||alpha_h||, 0) (0 when
@@ -148,6 +180,11 @@ cbct_status cbct_tf_analyze(int nx, int ny, int nz, const float *f, float *alpha
 cbct_status cbct_tf_synthesize_shrink(int nx, int ny, int nz, const float *alpha27,
                                       float mu, int positivity, float *f,
                                       cbct_stream_t stream);
+
+/* cbct_tf_synthesize_shrink reading coefficients stored as a_type (widened to FP32). */
+cbct_status cbct_tf_synthesize_shrink_ex(int nx, int ny, int nz, const void *alpha27,
+                                         cbct_dtype a_type, float mu, int positivity,
+                                         float *f, cbct_stream_t stream);
 
 /*
  * The regularisation step of Algorithms A1/A2 in one pass: f_out = H(W^T T_mu W f)

@@ -74,10 +74,13 @@ def _load():
                 "o_tf_shrink": (None, [ctypes.c_int] * 3 + [_P, ctypes.c_double]),
                 "o_positivity": (None, [ctypes.c_long, _P]),
                 "o_cgls": (None, [G, _P, _P, ctypes.c_int, _P]),
+                "o_cgls_storage": (None, [G, _P, _P, ctypes.c_int, _P, ctypes.c_int]),
+                "o_round_storage": (None, [ctypes.c_long, _P, ctypes.c_int]),
                 "o_a2": (None, [G, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
                 "o_prolong": (None, [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [_P] + [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [_P]),
                 "o_restrict": (None, [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [_P] + [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [_P]),
                 "o_reconstruct": (None, [G, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+                "o_reconstruct_storage": (None, [G, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
                 "o_num_threads": (ctypes.c_int, []),
             }
             for name, (res, args) in sig.items():
@@ -227,13 +230,31 @@ def tf_synthesize_shrink(alpha, mu, positive):
     return positivity(f) if positive else f
 
 
-def cgls(geom, y, x0, n_iter, return_resid=False):
-    """n_iter CGLS updates from x0 (Appendix 1). Returns x (and ||r||^2 history)."""
+# storage codes of the reduced-precision variant: 0 none (FP64), 1 bfloat16, 2 binary16
+STORAGE = {"f32": 0, "f64": 0, "bf16": 1, "f16": 2}
+
+
+def _storage(storage) -> int:
+    return STORAGE[storage] if isinstance(storage, str) else int(storage)
+
+
+def round_storage(x, storage):
+    """Round every value to the 16-bit storage format (nearest, ties to even)."""
+    lib = _load()
+    a = np.array(x, dtype=np.float64, copy=True)
+    flat = np.ascontiguousarray(a.ravel())
+    lib.o_round_storage(flat.size, _ptr(flat), _storage(storage))
+    return flat.reshape(a.shape)
+
+
+def cgls(geom, y, x0, n_iter, return_resid=False, storage=0):
+    """n_iter CGLS updates from x0 (Appendix 1). Returns x (and ||r||^2 history).
+    storage 'bf16' / 'f16' holds r and q in that 16-bit format (reduced-precision variant)."""
     lib = _load(); gh = _GeomHolder(geom)
     y = _f64(y, geom.proj_shape)
     x = _f64(x0, geom.vol_shape).copy()
     res = np.empty(n_iter + 1)
-    lib.o_cgls(gh.ref(), _ptr(y), _ptr(x), int(n_iter), _ptr(res))
+    lib.o_cgls_storage(gh.ref(), _ptr(y), _ptr(x), int(n_iter), _ptr(res), _storage(storage))
     return (x, res) if return_resid else x
 
 
@@ -273,14 +294,15 @@ def restrict(ff, fine_spacing, coarse_shape, coarse_spacing):
     return out
 
 
-def reconstruct(geom, y, mu, levels, iters, n_cgls=3, positivity=True, momentum=True):
-    """Multigrid A2 reconstruction (Section 2.2.3); iters coarsest first."""
+def reconstruct(geom, y, mu, levels, iters, n_cgls=3, positivity=True, momentum=True, storage=0):
+    """Multigrid A2 reconstruction (Section 2.2.3); iters coarsest first. storage selects
+    the reduced-precision CGLS variant ('bf16' / 'f16'; 0 = plain FP64)."""
     lib = _load(); gh = _GeomHolder(geom)
     y = _f64(y, geom.proj_shape)
     it = (ctypes.c_int * levels)(*[int(v) for v in iters])
     out = np.empty(geom.vol_shape)
-    lib.o_reconstruct(gh.ref(), _ptr(y), float(mu), int(levels), it, int(n_cgls),
-                      int(bool(positivity)), int(bool(momentum)), _ptr(out))
+    lib.o_reconstruct_storage(gh.ref(), _ptr(y), float(mu), int(levels), it, int(n_cgls),
+                              int(bool(positivity)), int(bool(momentum)), _storage(storage), _ptr(out))
     return out
 
 

@@ -62,10 +62,48 @@ def system_matrix(geom) -> np.ndarray:
     return A
 
 
-def cgls_dense(A, y, x0, n_iter):
-    """Appendix 1 CGLS on a dense matrix (the same listing, numpy vectors)."""
+def format_codes(fmt: str):
+    """Every finite value of a 16-bit format, sorted, with its bit pattern: decoded from
+    all 2^16 codes (binary16 via numpy's float16 view; bfloat16 as the high half of a
+    binary32 pattern)."""
+    codes = np.arange(1 << 16, dtype=np.uint32)
+    with np.errstate(invalid="ignore"):  # the NaN codes decode to NaN and are dropped below
+        if fmt == "f16":
+            vals = codes.astype(np.uint16).view(np.float16).astype(np.float64)
+        elif fmt == "bf16":
+            vals = (codes << 16).view(np.float32).astype(np.float64)
+        else:
+            raise ValueError(fmt)
+    keep = np.isfinite(vals) & ~((vals == 0) & (codes >= 0x8000))  # drop -0 and non-finite
+    order = np.argsort(vals[keep], kind="stable")
+    return vals[keep][order], codes[keep][order]
+
+
+def round_nearest_even(x, fmt: str):
+    """Brute-force rounding to a 16-bit format: the nearest finite value, ties to the
+    code with an even last bit; beyond the largest value by half its spacing or more,
+    infinity. A search over all codes, independent of any exponent arithmetic."""
+    vals, codes = format_codes(fmt)
+    x = np.asarray(x, dtype=np.float64)
+    top_gap = vals[-1] - vals[-2]
+    ext = np.concatenate([[-vals[-1] - top_gap], vals, [vals[-1] + top_gap]])  # +-inf stand-ins
+    ext_codes = np.concatenate([[0], codes, [0]])  # infinities' codes end in 0 (even)
+    i = np.clip(np.searchsorted(ext, x), 1, len(ext) - 1)
+    lo, hi = ext[i - 1], ext[i]
+    dlo, dhi = x - lo, hi - x
+    pick_hi = (dhi < dlo) | ((dhi == dlo) & (ext_codes[i] % 2 == 0))
+    out = np.where(pick_hi, hi, lo)
+    out = np.where(out > vals[-1], np.inf, np.where(out < vals[0], -np.inf, out))
+    return np.where(x == 0, x, out)
+
+
+def cgls_dense(A, y, x0, n_iter, storage=None):
+    """Appendix 1 CGLS on a dense matrix (the same listing, numpy vectors). storage
+    'bf16' / 'f16': r and q held in that format (rounded by round_nearest_even where
+    formed; binary16 holds q / sqrt(gamma))."""
+    rnd = (lambda v: v) if storage is None else (lambda v: round_nearest_even(v, storage))
     x = x0.astype(np.float64).copy()
-    r = y - A @ x
+    r = rnd(y - A @ x)
     s = A.T @ r
     p = s.copy()
     gamma = s @ s
@@ -76,7 +114,8 @@ def cgls_dense(A, y, x0, n_iter):
             break
         alpha = gamma / delta
         x += alpha * p
-        r -= alpha * q
+        kappa = 1.0 / np.sqrt(gamma) if storage == "f16" else 1.0
+        r = rnd(r - (alpha / kappa) * rnd(kappa * q))
         s = A.T @ r
         gnew = s @ s
         p = s + (gnew / gamma) * p

@@ -568,6 +568,36 @@ static double dot(long n, const double *a, const double *b)
 }
 
 /*
+ * Rounding to a 16-bit storage format, round to nearest with ties to even, written from
+ * the formats' definitions. storage 1 = bfloat16 (8 significand bits, the exponent range
+ * of binary32: smallest normal 2^-126, largest finite (2 - 2^-7) 2^127); storage 2 = IEEE
+ * binary16 (11 significand bits, smallest normal 2^-14, largest finite 65504); below the
+ * smallest normal the spacing is fixed (subnormals). Values beyond the largest finite
+ * number by half a spacing or more become infinite. storage 0 returns x unchanged.
+ * Pinned by: brute-force nearest-even search over all 2^16 codes of each format, and
+ * numpy's binary16 conversion (tests).
+ */
+static double round_storage(double x, int storage)
+{
+    if (storage == 0 || x == 0.0 || !isfinite(x)) return x;
+    const int p = storage == 1 ? 8 : 11;          /* significand bits */
+    const int emin = storage == 1 ? -126 : -14;   /* exponent of the smallest normal */
+    const double maxv = storage == 1 ? ldexp(2.0 - ldexp(1.0, -7), 127) : 65504.0;
+    int e;
+    frexp(x, &e);                /* 2^(e-1) <= |x| < 2^e */
+    int q = (e - 1) - (p - 1);   /* exponent of the spacing at |x| */
+    if (e - 1 < emin) q = emin - (p - 1);
+    double r = ldexp(nearbyint(ldexp(x, -q)), q); /* default mode: nearest, ties to even */
+    if (fabs(r) > maxv) return copysign(INFINITY, x);
+    return r;
+}
+
+void o_round_storage(long n, double *x, int storage)
+{
+    for (long i = 0; i < n; i++) x[i] = round_storage(x[i], storage);
+}
+
+/*
  * CGLS for min ||P x - y||^2 (Appendix 1) from the initial guess in x:
  *   r = y - P x, p = s = P^T r, gamma = ||s||^2; then n_iter times:
  *   q = P p, alpha = gamma / ||q||^2, x += alpha p, r -= alpha q, s = P^T r,
@@ -577,14 +607,22 @@ static double dot(long n, const double *a, const double *b)
  * resid (optional, n_iter+1 entries) receives ||r||^2 before and after every update.
  * Pinned by: the exact Krylov-subspace least-squares minimiser on small dense systems,
  * monotone residual (tests).
+ *
+ * storage != 0 is the reduced-precision variant (no counterpart in the paper): the
+ * projection-domain vectors r and q are held in a 16-bit format (round_storage) and all
+ * else is unchanged. r is rounded where it is formed and after every update; q is
+ * rounded after ||q||^2 is taken from the unrounded values. For binary16 q is held as
+ * kappa q with kappa = 1 / sqrt(gamma) (keeps it in range) and the update reads
+ * r -= (alpha / kappa) (kappa q). Pinned by: a dense-matrix restatement that rounds
+ * through a brute-force nearest-even search (tests).
  */
-void o_cgls(const og_geom *g, const double *y, double *x, int n_iter, double *resid)
+static void cgls_impl(const og_geom *g, const double *y, double *x, int n_iter, double *resid, int storage)
 {
     long N = (long)g->nx * g->ny * g->nz, M = (long)g->n_views * g->nv * g->nu;
     double *r = (double *)malloc(sizeof(double) * M), *q = (double *)malloc(sizeof(double) * M);
     double *s = (double *)malloc(sizeof(double) * N), *p = (double *)malloc(sizeof(double) * N);
     o_project(g, x, r);
-    for (long i = 0; i < M; i++) r[i] = y[i] - r[i];
+    for (long i = 0; i < M; i++) r[i] = round_storage(y[i] - r[i], storage);
     o_backproject(g, r, s);
     memcpy(p, s, sizeof(double) * N);
     double gamma = dot(N, s, s);
@@ -602,7 +640,15 @@ void o_cgls(const og_geom *g, const double *y, double *x, int n_iter, double *re
         }
         double alpha = gamma / delta;
         for (long j = 0; j < N; j++) x[j] += alpha * p[j];
-        for (long i = 0; i < M; i++) r[i] -= alpha * q[i];
+        if (storage == 0) {
+            for (long i = 0; i < M; i++) r[i] -= alpha * q[i];
+        } else {
+            const double kappa = storage == 2 ? 1.0 / sqrt(gamma) : 1.0;
+            for (long i = 0; i < M; i++) {
+                const double qs = round_storage(kappa * q[i], storage);
+                r[i] = round_storage(r[i] - (alpha / kappa) * qs, storage);
+            }
+        }
         if (resid) resid[l + 1] = dot(M, r, r);
         o_backproject(g, r, s);
         double gnew = dot(N, s, s);
@@ -613,16 +659,27 @@ void o_cgls(const og_geom *g, const double *y, double *x, int n_iter, double *re
     free(r); free(q); free(s); free(p);
 }
 
+void o_cgls(const og_geom *g, const double *y, double *x, int n_iter, double *resid)
+{
+    cgls_impl(g, y, x, n_iter, resid, 0);
+}
+
+void o_cgls_storage(const og_geom *g, const double *y, double *x, int n_iter, double *resid, int storage)
+{
+    cgls_impl(g, y, x, n_iter, resid, storage);
+}
+
 /*
  * Algorithm A2 (Section 2.1) on one grid, n_outer iterations. f holds f^(0) on entry
  * (f^(-1) = f^(0), t^(0) = t^(-1) = 1) and f^(n_outer) on exit:
  *   v = f^(k) + (t^(k-1) - 1) / t^(k) (f^(k) - f^(k-1));   [momentum = 0: v = f^(k), i.e. A1]
  *   f^(k+1) = CGLS[v];  f^(k+1) <- D^T T_mu D f^(k+1);  f^(k+1) <- H f^(k+1)  [if positivity];
  *   t^(k+1) = (1 + sqrt(1 + 4 t^(k)^2)) / 2.
- * Parity of the iteration as a whole is pinned only through special cases (tests).
+ * storage selects the CGLS variant above. Parity of the iteration as a whole is pinned
+ * only through special cases (tests).
  */
-void o_a2(const og_geom *g, const double *y, double mu, int n_outer, int n_cgls, int positivity,
-          int momentum, double *f)
+static void a2_impl(const og_geom *g, const double *y, double mu, int n_outer, int n_cgls, int positivity,
+                    int momentum, int storage, double *f)
 {
     long N = (long)g->nx * g->ny * g->nz;
     double *fprev = (double *)malloc(sizeof(double) * N);
@@ -633,7 +690,7 @@ void o_a2(const og_geom *g, const double *y, double mu, int n_outer, int n_cgls,
     for (int k = 0; k < n_outer; k++) {
         double c = momentum ? (t_prev - 1.0) / t : 0.0;
         for (long j = 0; j < N; j++) x[j] = f[j] + c * (f[j] - fprev[j]);
-        o_cgls(g, y, x, n_cgls, NULL);
+        cgls_impl(g, y, x, n_cgls, NULL, storage);
         o_tf_analyze(g->nx, g->ny, g->nz, x, alpha);
         o_tf_shrink(g->nx, g->ny, g->nz, alpha, mu);
         o_tf_synthesize(g->nx, g->ny, g->nz, alpha, x);
@@ -645,6 +702,12 @@ void o_a2(const og_geom *g, const double *y, double mu, int n_outer, int n_cgls,
         t = t_next;
     }
     free(fprev); free(x); free(alpha);
+}
+
+void o_a2(const og_geom *g, const double *y, double mu, int n_outer, int n_cgls, int positivity,
+          int momentum, double *f)
+{
+    a2_impl(g, y, mu, n_outer, n_cgls, positivity, momentum, 0, f);
 }
 
 /*
@@ -724,8 +787,8 @@ void o_restrict(int nx, int ny, int nz, double dx, double dy, double dz, const d
  * result as the initial guess of the next finer grid, and so on. iters[] lists the A2
  * iteration counts coarsest first.
  */
-void o_reconstruct(const og_geom *g, const double *y, double mu, int levels, const int *iters,
-                   int n_cgls, int positivity, int momentum, double *f_out)
+static void reconstruct_impl(const og_geom *g, const double *y, double mu, int levels, const int *iters,
+                             int n_cgls, int positivity, int momentum, int storage, double *f_out)
 {
     double *fc = NULL;
     og_geom prev = *g;
@@ -741,12 +804,25 @@ void o_reconstruct(const og_geom *g, const double *y, double mu, int levels, con
                       gl.nx, gl.ny, gl.nz, gl.dx, gl.dy, gl.dz, f);
             free(fc);
         }
-        o_a2(&gl, y, mu, iters[levels - 1 - lev], n_cgls, positivity, momentum, f);
+        a2_impl(&gl, y, mu, iters[levels - 1 - lev], n_cgls, positivity, momentum, storage, f);
         fc = f;
         prev = gl;
     }
     memcpy(f_out, fc, sizeof(double) * (long)g->nx * g->ny * g->nz);
     free(fc);
+}
+
+void o_reconstruct(const og_geom *g, const double *y, double mu, int levels, const int *iters,
+                   int n_cgls, int positivity, int momentum, double *f_out)
+{
+    reconstruct_impl(g, y, mu, levels, iters, n_cgls, positivity, momentum, 0, f_out);
+}
+
+/* o_reconstruct with the reduced-precision CGLS variant (storage 1 = bfloat16, 2 = binary16). */
+void o_reconstruct_storage(const og_geom *g, const double *y, double mu, int levels, const int *iters,
+                           int n_cgls, int positivity, int momentum, int storage, double *f_out)
+{
+    reconstruct_impl(g, y, mu, levels, iters, n_cgls, positivity, momentum, storage, f_out);
 }
 
 int o_num_threads(void)

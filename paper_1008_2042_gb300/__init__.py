@@ -6,8 +6,9 @@ the current stream. There is no CPU fallback: if the library is missing or no GP
 present, calls raise.
 
 Layouts follow the C ABI: volumes (nz, ny, nx) float32, projection stacks
-(n_views, nv, nu) float32, frame coefficients (27, nz, ny, nx) float32, all contiguous
-CUDA tensors on the device the geometry was created on.
+(n_views, nv, nu), frame coefficients (27, nz, ny, nx), all contiguous CUDA tensors on
+the device the geometry was created on. Projection stacks and frame coefficients may be
+float32, bfloat16 or float16 (storage only: the arithmetic is FP32).
 """
 from __future__ import annotations
 
@@ -42,7 +43,26 @@ class GeometryDesc(ctypes.Structure):
 
 
 class ReconOpts(ctypes.Structure):
-    _fields_ = [("n_cgls", ctypes.c_int), ("momentum", ctypes.c_int), ("positivity", ctypes.c_int)]
+    _fields_ = [("n_cgls", ctypes.c_int), ("momentum", ctypes.c_int), ("positivity", ctypes.c_int),
+                ("storage", ctypes.c_int)]
+
+
+# cbct_dtype codes of the storage types
+DTYPES = {torch.float32: 0, torch.bfloat16: 1, torch.float16: 2}
+_DTYPE_NAMES = {"f32": torch.float32, "fp32": torch.float32, "float32": torch.float32,
+                "bf16": torch.bfloat16, "bfloat16": torch.bfloat16,
+                "f16": torch.float16, "fp16": torch.float16, "float16": torch.float16}
+
+
+def storage_dtype(d) -> torch.dtype:
+    """A storage type given as a torch dtype or a name ('f32', 'bf16', 'f16')."""
+    if isinstance(d, str):
+        if d.lower() not in _DTYPE_NAMES:
+            raise ValueError(f"unknown storage type {d!r}")
+        return _DTYPE_NAMES[d.lower()]
+    if d not in DTYPES:
+        raise ValueError(f"unsupported storage type {d}")
+    return d
 
 
 _vp = ctypes.c_void_p
@@ -56,6 +76,10 @@ _SIGNATURES = {
     "cbct_project": [_vp, _vp, _vp, _vp],
     "cbct_project_static": [_vp, _vp, _vp, _vp],
     "cbct_backproject": [_vp, _vp, _vp, _vp],
+    "cbct_project_ex": [_vp, _vp, _vp, _i, _vp],
+    "cbct_backproject_ex": [_vp, _vp, _i, _vp, _vp],
+    "cbct_tf_analyze_ex": [_i, _i, _i, _vp, _vp, _i, _vp],
+    "cbct_tf_synthesize_shrink_ex": [_i, _i, _i, _vp, _i, _f, _i, _vp, _vp],
     "cbct_backproject_eq3": [_vp, _vp, _vp, _vp],
     "cbct_project_batch": [_vp, _i, _vp, _vp, _vp],
     "cbct_backproject_batch": [_vp, _i, _vp, _vp, _vp],
@@ -109,10 +133,13 @@ def _stream(stream: Optional[torch.cuda.Stream]):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _dev(t: torch.Tensor, shape, name: str) -> ctypes.c_void_p:
+def _dev(t: torch.Tensor, shape, name: str, typed: bool = False) -> ctypes.c_void_p:
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
-    if t.dtype != torch.float32 or not t.is_contiguous():
+    if typed:
+        if t.dtype not in DTYPES or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous float32, bfloat16 or float16 tensor")
+    elif t.dtype != torch.float32 or not t.is_contiguous():
         raise TypeError(f"{name} must be a contiguous float32 tensor")
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
@@ -187,12 +214,19 @@ class Geometry:
         self.close()
 
 
-def project(geom: Geometry, f: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
-    """g = P f (Siddon forward projection)."""
+def project(geom: Geometry, f: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None,
+            dtype=torch.float32) -> torch.Tensor:
+    """g = P f (Siddon forward projection). The projections are stored as `out.dtype` when
+    `out` is given, else as `dtype` (float32, bfloat16 or float16)."""
     if out is None:
-        out = torch.empty(geom.proj_shape, dtype=torch.float32, device=f.device)
-    _check(load_library().cbct_project(geom.handle, _dev(f, geom.vol_shape, "f"),
-                                       _dev(out, geom.proj_shape, "out"), _stream(stream)))
+        out = torch.empty(geom.proj_shape, dtype=storage_dtype(dtype), device=f.device)
+    po = _dev(out, geom.proj_shape, "out", typed=True)
+    lib = load_library()
+    if out.dtype == torch.float32:
+        _check(lib.cbct_project(geom.handle, _dev(f, geom.vol_shape, "f"), po, _stream(stream)))
+    else:
+        _check(lib.cbct_project_ex(geom.handle, _dev(f, geom.vol_shape, "f"), po, DTYPES[out.dtype],
+                                   _stream(stream)))
     return out
 
 
@@ -206,11 +240,16 @@ def project_static(geom: Geometry, f: torch.Tensor, out: torch.Tensor, stream=No
 
 
 def backproject(geom: Geometry, g: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
-    """f = P^T g (exact adjoint)."""
+    """f = P^T g (exact adjoint); g may be float32, bfloat16 or float16."""
     if out is None:
         out = torch.empty(geom.vol_shape, dtype=torch.float32, device=g.device)
-    _check(load_library().cbct_backproject(geom.handle, _dev(g, geom.proj_shape, "g"),
-                                           _dev(out, geom.vol_shape, "out"), _stream(stream)))
+    pg = _dev(g, geom.proj_shape, "g", typed=True)
+    lib = load_library()
+    if g.dtype == torch.float32:
+        _check(lib.cbct_backproject(geom.handle, pg, _dev(out, geom.vol_shape, "out"), _stream(stream)))
+    else:
+        _check(lib.cbct_backproject_ex(geom.handle, pg, DTYPES[g.dtype], _dev(out, geom.vol_shape, "out"),
+                                       _stream(stream)))
     return out
 
 
@@ -243,25 +282,35 @@ def backproject_batch(geom: Geometry, g: torch.Tensor, out: Optional[torch.Tenso
     return out
 
 
-def tf_analyze(f: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
-    """alpha = W f, 27 channels."""
+def tf_analyze(f: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None, dtype=torch.float32) -> torch.Tensor:
+    """alpha = W f, 27 channels, stored as `out.dtype` (or `dtype` when out is None)."""
     nz, ny, nx = f.shape
     if out is None:
-        out = torch.empty((27, nz, ny, nx), dtype=torch.float32, device=f.device)
-    _check(load_library().cbct_tf_analyze(nx, ny, nz, _dev(f, None, "f"),
-                                          _dev(out, (27, nz, ny, nx), "out"), _stream(stream)))
+        out = torch.empty((27, nz, ny, nx), dtype=storage_dtype(dtype), device=f.device)
+    pa = _dev(out, (27, nz, ny, nx), "out", typed=True)
+    lib = load_library()
+    if out.dtype == torch.float32:
+        _check(lib.cbct_tf_analyze(nx, ny, nz, _dev(f, None, "f"), pa, _stream(stream)))
+    else:
+        _check(lib.cbct_tf_analyze_ex(nx, ny, nz, _dev(f, None, "f"), pa, DTYPES[out.dtype], _stream(stream)))
     return out
 
 
 def tf_synthesize_shrink(alpha: torch.Tensor, mu: float, positivity: bool = True,
                          out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
-    """f = H(W^T T_mu alpha) (H only if positivity)."""
+    """f = H(W^T T_mu alpha) (H only if positivity); alpha may be float32, bfloat16 or float16."""
     _, nz, ny, nx = alpha.shape
     if out is None:
         out = torch.empty((nz, ny, nx), dtype=torch.float32, device=alpha.device)
-    _check(load_library().cbct_tf_synthesize_shrink(nx, ny, nz, _dev(alpha, None, "alpha"), float(mu),
-                                                    int(bool(positivity)), _dev(out, (nz, ny, nx), "out"),
-                                                    _stream(stream)))
+    pa = _dev(alpha, None, "alpha", typed=True)
+    lib = load_library()
+    if alpha.dtype == torch.float32:
+        _check(lib.cbct_tf_synthesize_shrink(nx, ny, nz, pa, float(mu), int(bool(positivity)),
+                                             _dev(out, (nz, ny, nx), "out"), _stream(stream)))
+    else:
+        _check(lib.cbct_tf_synthesize_shrink_ex(nx, ny, nz, pa, DTYPES[alpha.dtype], float(mu),
+                                                int(bool(positivity)), _dev(out, (nz, ny, nx), "out"),
+                                                _stream(stream)))
     return out
 
 
@@ -286,15 +335,17 @@ def cgls(geom: Geometry, y: torch.Tensor, x: torch.Tensor, n_iter: int, stream=N
 def reconstruct(geom: Geometry, y: torch.Tensor, mu: float, levels: int, iters: Sequence[int],
                 lam: float = 0.0, n_cgls: int = 3, momentum: bool = True, positivity: bool = True,
                 workspace: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
-                stream=None) -> torch.Tensor:
-    """Multigrid A2 reconstruction; iters lists the outer iterations per level, coarsest first."""
+                stream=None, storage=torch.float32) -> torch.Tensor:
+    """Multigrid A2 reconstruction; iters lists the outer iterations per level, coarsest first.
+    `storage` is the type of the CGLS residual and projected direction (float32, bfloat16,
+    float16, or 'f32' / 'bf16' / 'f16')."""
     lib = load_library()
     if len(iters) != levels:
         raise ValueError("iters must have one entry per level")
     if out is None:
         out = torch.empty(geom.vol_shape, dtype=torch.float32, device=y.device)
     it = (ctypes.c_int * levels)(*[int(v) for v in iters])
-    opts = ReconOpts(int(n_cgls), int(bool(momentum)), int(bool(positivity)))
+    opts = ReconOpts(int(n_cgls), int(bool(momentum)), int(bool(positivity)), DTYPES[storage_dtype(storage)])
     ws, ws_bytes = None, 0
     if workspace is not None:
         if not workspace.is_cuda or not workspace.is_contiguous():

@@ -249,8 +249,9 @@ cbct_status launch_backproject(const GeomDev &G, const float2 *ps, float *out, l
 // pass 1 sums each chunk, the chunk offsets come from shared memory, pass 2 writes.
 constexpr int PREFIX_WARPS = 16;
 
+template <typename T>
 __global__ void __launch_bounds__(32 * PREFIX_WARPS)
-k_row_prefix(GeomDev G, const float *__restrict__ g, float2 *__restrict__ ps, int prescale)
+k_row_prefix(GeomDev G, const T *__restrict__ g, float2 *__restrict__ ps, int prescale)
 {
     __shared__ double s_tot[PREFIX_WARPS][32];
     const int lane = threadIdx.x, w = threadIdx.y;
@@ -264,11 +265,11 @@ k_row_prefix(GeomDev G, const float *__restrict__ g, float2 *__restrict__ ps, in
         dxr = r4.x;
         dyr = r4.y;
     }
-    const float *src = g + (size_t)k * G.nv * G.nu + iu;
+    const T *src = g + (size_t)k * G.nv * G.nu + iu;
     double t = 0.0;
     if (ok)
         for (int iv = r0; iv < r1; ++iv) {
-            float val = __ldg(src + (size_t)iv * G.nu);
+            float val = load_as_float(src + (size_t)iv * G.nu);
             if (prescale) val *= ray_length(dxr, dyr, imager_v(G, iv));
             t += (double)val;
         }
@@ -280,7 +281,7 @@ k_row_prefix(GeomDev G, const float *__restrict__ g, float2 *__restrict__ ps, in
     float2 *dst = ps + ((size_t)k * G.nu + iu) * ((size_t)G.nv + 1);
     if (w == 0) dst[0] = make_float2(0.0f, 0.0f);
     for (int iv = r0; iv < r1; ++iv) {
-        float val = __ldg(src + (size_t)iv * G.nu);
+        float val = load_as_float(src + (size_t)iv * G.nu);
         if (prescale) val *= ray_length(dxr, dyr, imager_v(G, iv));
         run += (double)val;
         const float hi = (float)run;
@@ -288,13 +289,20 @@ k_row_prefix(GeomDev G, const float *__restrict__ g, float2 *__restrict__ ps, in
     }
 }
 
-cbct_status launch_row_prefix(const GeomDev &G, const float *g, float2 *ps, int prescale, cudaStream_t st)
+cbct_status launch_row_prefix(const GeomDev &G, const void *g, float2 *ps, int prescale, cudaStream_t st, int storage)
 {
     dim3 grid((G.nu + 31) / 32, G.nviews), block(32, PREFIX_WARPS);
-    CBCT_TIMED(CBCT_KERNEL_OTHER, st, k_row_prefix<<<grid, block, 0, st>>>(G, g, ps, prescale));
+    if (storage == ST_BF16)
+        CBCT_TIMED(CBCT_KERNEL_OTHER, st,
+                   k_row_prefix<__nv_bfloat16><<<grid, block, 0, st>>>(G, static_cast<const __nv_bfloat16 *>(g), ps, prescale));
+    else if (storage == ST_F16)
+        CBCT_TIMED(CBCT_KERNEL_OTHER, st,
+                   k_row_prefix<__half><<<grid, block, 0, st>>>(G, static_cast<const __half *>(g), ps, prescale));
+    else
+        CBCT_TIMED(CBCT_KERNEL_OTHER, st,
+                   k_row_prefix<float><<<grid, block, 0, st>>>(G, static_cast<const float *>(g), ps, prescale));
     return check_cuda(cudaGetLastError(), "row prefix launch");
 }
-
 
 // The paper's own backprojector, Eq. (3): voxel-driven, for every view the imager value at
 // the point u* where the ray through the voxel centre x meets the imager is taken by

@@ -8,6 +8,10 @@
 //   projection stacks are always [n_views][nv][nu].
 #pragma once
 
+#include <atomic>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -81,6 +85,51 @@ __device__ __forceinline__ float ray_length(float dxr, float dyr, float v)
     return sqrtf(fmaf(dxr, dxr, fmaf(dyr, dyr, v * v)));
 }
 
+// Storage type of the projection-domain working vectors (y, r, q) and of stored frame
+// coefficients: FP32, BF16 or FP16. Arithmetic is always FP32 (FP64 for inner products).
+enum StorageType { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2 };
+
+template <typename T> __device__ __forceinline__ float load_as_float(const T *p);
+template <> __device__ __forceinline__ float load_as_float<float>(const float *p) { return __ldg(p); }
+template <> __device__ __forceinline__ float load_as_float<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    return __bfloat162float(__ldg(p));
+}
+template <> __device__ __forceinline__ float load_as_float<__half>(const __half *p) { return __half2float(__ldg(p)); }
+template <typename T> __device__ __forceinline__ void store_from_float(T *p, float v);
+template <> __device__ __forceinline__ void store_from_float<float>(float *p, float v) { *p = v; }
+template <> __device__ __forceinline__ void store_from_float<__nv_bfloat16>(__nv_bfloat16 *p, float v)
+{
+    *p = __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ void store_from_float<__half>(__half *p, float v) { *p = __float2half_rn(v); }
+
+// streaming (evict-first) store of a value that is not read again by this kernel
+template <typename T> __device__ __forceinline__ void store_stream(T *p, float v);
+template <> __device__ __forceinline__ void store_stream<float>(float *p, float v) { __stcs(p, v); }
+template <> __device__ __forceinline__ void store_stream<__nv_bfloat16>(__nv_bfloat16 *p, float v)
+{
+    __stcs(p, __float2bfloat16_rn(v));
+}
+template <> __device__ __forceinline__ void store_stream<__half>(__half *p, float v) { __stcs(p, __float2half_rn(v)); }
+
+static inline size_t storage_bytes(int storage) { return storage == ST_F32 ? 4 : 2; }
+
+// Opts a kernel into more than 48 KB of dynamic shared memory. The attribute belongs to
+// the function on one device, so it is set once per device (`done` holds one bit each).
+template <typename Kernel>
+inline cudaError_t smem_optin_once(Kernel *fn, int bytes, std::atomic<unsigned long long> &done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load() & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.fetch_or(bit);
+    return e;
+}
+
 // Device-resident scalars of CGLS (Appendix 1), FP64.
 struct Scalars {
     double gamma;    // ||s||^2
@@ -88,17 +137,18 @@ struct Scalars {
     double alpha;    // gamma / delta
     double beta;     // gamma' / gamma
     double rr;       // ||r||^2 (monitoring)
+    double kappa;    // q is stored as kappa * q, kappa = 1 / sqrt(gamma): keeps FP16 in range
     unsigned int flags; // bit 0: a reduction was not finite
     unsigned int pad;
 };
 
 enum FinalizeOp { FIN_GAMMA = 0, FIN_ALPHA = 1, FIN_BETA = 2, FIN_RR = 3 };
 
-// Projector epilogues.
+// Projector epilogues (q = |D - S| * sum of f * dtau is the projection of the ray).
 enum ProjectMode {
-    PM_PLAIN = 0,      // out = |d| S                     (public P)
-    PM_Q_PRESCALED = 1,// out = |d| * q, q = |d| S; partial sums of q^2
-    PM_R_PRESCALED = 2,// out = |d| * (y - q); partial sums of (y - q)^2
+    PM_PLAIN = 0,      // out = q                                     (public P)
+    PM_Q_SCALED = 1,   // out = kappa * q (stored type), partial sums of q^2
+    PM_RESID = 2,      // out = y - q (stored type), partial sums of (y - q)^2
     PM_COUNT = 3       // count segments longer than a threshold
 };
 
@@ -130,24 +180,28 @@ int device_sm_count();
 // Launchers (all asynchronous on `st`; return CBCT_ERR_CUDA on launch failure).
 // Volume element (ix, iy, iz) lives at ix*sx + iy*sy + iz*sz.
 int project_num_blocks(const GeomDev &G);
+// out holds `storage`-typed values (PM_COUNT: none); y is FP32; sc supplies kappa in
+// PM_Q_SCALED. With FP32 storage the CGLS modes store |D - S| r and |D - S| q.
 cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long long sy,
-                           long long sz, const float *y, float *out, int mode,
-                           double *partials, float count_thr, cudaStream_t st);
+                           long long sz, const float *y, void *out, int mode,
+                           double *partials, float count_thr, cudaStream_t st,
+                           int storage = ST_F32, const Scalars *sc = nullptr);
 int backproject_num_blocks(const GeomDev &G);
 // ps: per-(view, imager column) prefix sums over rows of the |D - S|-weighted stack,
 // [n_views][nu][nv + 1] float2 (hi, lo), built by launch_row_prefix.
 cbct_status launch_backproject(const GeomDev &G, const float2 *ps, float *out, long long sx,
                                long long sy, long long sz, float *out2, double *partials,
                                cudaStream_t st);
-cbct_status launch_row_prefix(const GeomDev &G, const float *g, float2 *ps, int prescale,
-                              cudaStream_t st);
+cbct_status launch_row_prefix(const GeomDev &G, const void *g, float2 *ps, int prescale,
+                              cudaStream_t st, int storage = ST_F32);
 cbct_status launch_backproject_eq3(const GeomDev &G, const float *g, float *f, float pref,
                                    cudaStream_t st);
 
-cbct_status launch_tf_analyze(int n0, int n1, int n2, const float *f, float *alpha,
-                              cudaStream_t st);
-cbct_status launch_tf_synth_shrink(int n0, int n1, int n2, const float *alpha, float mu,
-                                   int positivity, float *f, cudaStream_t st);
+// alpha holds `storage`-typed coefficients (FP32, BF16 or FP16); arithmetic is FP32
+cbct_status launch_tf_analyze(int n0, int n1, int n2, const float *f, void *alpha,
+                              cudaStream_t st, int storage = ST_F32);
+cbct_status launch_tf_synth_shrink(int n0, int n1, int n2, const void *alpha, float mu,
+                                   int positivity, float *f, cudaStream_t st, int storage = ST_F32);
 // Fused f_new = H(W^T T_mu W x) and, if vout != nullptr, v = f_new + coef (f_new - f_old).
 cbct_status launch_tf_shrink_fused(int n0, int n1, int n2, const float *x, float mu, int positivity,
                                    float *fnew, const float *fold, float coef, float *vout,

@@ -12,7 +12,7 @@
 // unrolled groups whose loads are all in flight together; the rare columns in which a
 // lane crosses a z plane are corrected afterwards. Accumulation is FP32; the epilogue can
 // scale by |D - S|, form the CGLS residual and reduce squared norms in FP64 into one
-// partial per block.
+// partial per block; the output is stored as FP32, BF16 or FP16.
 #include <cfloat>
 
 #include "cbct_internal.cuh"
@@ -105,10 +105,10 @@ template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile(
 // reads the voxel pair (kb, kb + 1) around its current and next slab in every column and
 // splits each column's length at its crossing with a saturated FMA. No branch and no
 // integer or compare instruction is spent per column.
-template <int MODE>
+template <int MODE, typename TP>
 __global__ void __launch_bounds__(PROJ_THREADS, 4)
 k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *__restrict__ y,
-          float *__restrict__ out, double *__restrict__ partials, float count_thr)
+          TP *__restrict__ out, double *__restrict__ partials, float count_thr, const Scalars *__restrict__ sc)
 {
     extern __shared__ float smem[];
     __shared__ double s_warp[PROJ_THREADS / 32];
@@ -374,19 +374,24 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
 
     // ---- epilogue ----
     double red = 0.0;
+    const float kappa = (MODE == PM_Q_SCALED) ? (float)sc->kappa : 1.0f;
+    constexpr bool PRESCALE = sizeof(TP) == 4;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (!ok[r]) continue;
         const size_t idx = ((size_t)view * G.nv + iv[r]) * G.nu + iu;
         const float q = acc[r] * L[r];
+        // FP32 storage keeps |D - S| folded into r and q (the adjoint then needs no
+        // per-sample rescale); 16-bit storage keeps the bare values
+        const float s = PRESCALE ? L[r] : 1.0f;
         if (MODE == PM_PLAIN) {
-            out[idx] = q;
-        } else if (MODE == PM_Q_PRESCALED) {
-            out[idx] = q * L[r];
+            store_from_float(out + idx, q);
+        } else if (MODE == PM_Q_SCALED) {
+            store_from_float(out + idx, q * s * kappa);
             red += (double)q * (double)q;
-        } else if (MODE == PM_R_PRESCALED) {
-            const float rr = y[idx] - q;
-            out[idx] = rr * L[r];
+        } else if (MODE == PM_RESID) {
+            const float rr = __ldg(y + idx) - q;
+            store_from_float(out + idx, rr * s);
             red += (double)rr * (double)rr;
         }
     }
@@ -404,44 +409,59 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
     }
 }
 
-cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long long sy,
-                           long long sz, const float *y, float *out, int mode,
-                           double *partials, float count_thr, cudaStream_t st)
+template <int MODE, typename TP>
+static cbct_status launch_project_t(const GeomDev &G, const float *f, int isx, int isy, const float *y, void *out,
+                                   double *partials, float count_thr, const Scalars *sc, dim3 grid, int threads,
+                                   size_t smem, cudaStream_t st)
 {
-    const int rows = proj_threads(G); // threads per block; 2 rows each
-    dim3 grid((unsigned)(G.nviews * G.nu), (unsigned)((G.nv + 2 * rows - 1) / (2 * rows)));
+    static std::atomic<unsigned long long> done{0};
+    cudaError_t e = smem_optin_once(k_project<MODE, TP>, 200 * 1024, done);
+    if (e != cudaSuccess) return check_cuda(e, "project attribute");
+    k_project<MODE, TP><<<grid, threads, smem, st>>>(G, f, isx, isy, y, static_cast<TP *>(out),
+                                                    partials, count_thr, sc);
+    return CBCT_OK;
+}
+
+cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long long sy,
+                           long long sz, const float *y, void *out, int mode,
+                           double *partials, float count_thr, cudaStream_t st, int storage, const Scalars *sc)
+{
+    const int threads = proj_threads(G); // 2 rows each
+    dim3 grid((unsigned)(G.nviews * G.nu), (unsigned)((G.nv + 2 * threads - 1) / (2 * threads)));
     const size_t smem = project_smem(G);
     if (smem > 200 * 1024)
         return set_error(CBCT_ERR_UNSUPPORTED, "project: grid too large for the projector's shared memory (nx + ny and nz)");
-    static bool attr_set[4] = {false, false, false, false};
-    if (!attr_set[mode & 3]) {
-        const void *fn = mode == PM_PLAIN ? (const void *)k_project<PM_PLAIN>
-                       : mode == PM_Q_PRESCALED ? (const void *)k_project<PM_Q_PRESCALED>
-                       : mode == PM_R_PRESCALED ? (const void *)k_project<PM_R_PRESCALED>
-                                                : (const void *)k_project<PM_COUNT>;
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return check_cuda(e, "project attribute");
-        attr_set[mode & 3] = true;
-    }
     if (sz != 1) return set_error(CBCT_ERR_INVALID_ARG, "project: the volume must be z-contiguous");
     const int isx = (int)sx, isy = (int)sy;
+    cbct_status r = CBCT_OK;
     ProfToken tok = prof_start(CBCT_KERNEL_PROJECT, st);
-    switch (mode) {
-    case PM_PLAIN:
-        k_project<PM_PLAIN><<<grid, rows, smem, st>>>(G, f, isx, isy, y, out, partials, count_thr);
-        break;
-    case PM_Q_PRESCALED:
-        k_project<PM_Q_PRESCALED><<<grid, rows, smem, st>>>(G, f, isx, isy, y, out, partials, count_thr);
-        break;
-    case PM_R_PRESCALED:
-        k_project<PM_R_PRESCALED><<<grid, rows, smem, st>>>(G, f, isx, isy, y, out, partials, count_thr);
-        break;
-    default:
-        k_project<PM_COUNT><<<grid, rows, smem, st>>>(G, f, isx, isy, y, out, partials, count_thr);
-        break;
+    if (mode == PM_PLAIN) {
+        if (storage == ST_BF16)
+            r = launch_project_t<PM_PLAIN, __nv_bfloat16>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+        else if (storage == ST_F16)
+            r = launch_project_t<PM_PLAIN, __half>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+        else
+            r = launch_project_t<PM_PLAIN, float>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+    } else if (mode == PM_COUNT) {
+        r = launch_project_t<PM_COUNT, float>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+    } else if (mode == PM_Q_SCALED) {
+        if (storage == ST_BF16)
+            r = launch_project_t<PM_Q_SCALED, __nv_bfloat16>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+        else if (storage == ST_F16)
+            r = launch_project_t<PM_Q_SCALED, __half>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+        else
+            r = launch_project_t<PM_Q_SCALED, float>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+    } else {
+        if (storage == ST_BF16)
+            r = launch_project_t<PM_RESID, __nv_bfloat16>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+        else if (storage == ST_F16)
+            r = launch_project_t<PM_RESID, __half>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+        else
+            r = launch_project_t<PM_RESID, float>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
     }
     prof_stop(tok, st);
     note_launch();
+    if (r != CBCT_OK) return r;
     return check_cuda(cudaGetLastError(), "project launch");
 }
 

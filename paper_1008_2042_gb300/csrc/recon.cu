@@ -18,8 +18,10 @@ namespace cbct {
 // Reductions and vector updates
 // ------------------------------------------------------------------------------------
 
+// scale_q: q is about to be stored in FP16, so keep kappa = 1 / sqrt(gamma) (||kappa p|| >= 1
+// and kappa q stays O(1)); otherwise kappa = 1.
 __global__ void __launch_bounds__(1024) k_finalize(const double *__restrict__ partials, int n,
-                                                   Scalars *sc, int op)
+                                                   Scalars *sc, int op, int scale_q)
 {
     __shared__ double s[32];
     double t = 0.0;
@@ -32,23 +34,22 @@ __global__ void __launch_bounds__(1024) k_finalize(const double *__restrict__ pa
         double sum = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += s[w];
         if (!isfinite(sum)) sc->flags |= 1u;
-        if (op == FIN_GAMMA) {
+        if (op == FIN_GAMMA || op == FIN_BETA) {
+            if (op == FIN_BETA) sc->beta = sc->gamma > 0.0 ? sum / sc->gamma : 0.0;
             sc->gamma = sum;
+            sc->kappa = (scale_q && sum > 0.0 && isfinite(sum)) ? 1.0 / sqrt(sum) : 1.0;
         } else if (op == FIN_ALPHA) {
             sc->delta = sum;
             sc->alpha = (sc->gamma > 0.0 && sum > 0.0) ? sc->gamma / sum : 0.0;
-        } else if (op == FIN_BETA) {
-            sc->beta = sc->gamma > 0.0 ? sum / sc->gamma : 0.0;
-            sc->gamma = sum;
         } else {
             sc->rr = sum;
         }
     }
 }
 
-static cbct_status finalize(const double *partials, int n, Scalars *sc, int op, cudaStream_t st)
+static cbct_status finalize(const double *partials, int n, Scalars *sc, int op, cudaStream_t st, int scale_q = 0)
 {
-    CBCT_TIMED(CBCT_KERNEL_OTHER, st, k_finalize<<<1, 1024, 0, st>>>(partials, n, sc, op));
+    CBCT_TIMED(CBCT_KERNEL_OTHER, st, k_finalize<<<1, 1024, 0, st>>>(partials, n, sc, op, scale_q));
     return check_cuda(cudaGetLastError(), "finalize launch");
 }
 
@@ -61,24 +62,75 @@ static int vec_blocks(size_t n)
     return b < 1 ? 1 : (int)b;
 }
 
-// r -= alpha q
-__global__ void k_update_r(float *__restrict__ r, const float *__restrict__ q, const Scalars *sc, size_t n)
+// Four consecutive values as FP32 (one 16-byte or 8-byte load) and back.
+__device__ __forceinline__ float4 load4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void store4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float4 load4(const __nv_bfloat16 *p)
 {
-    const float a = (float)sc->alpha;
+    const uint2 raw = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void store4(__nv_bfloat16 *p, float4 v)
+{
+    uint2 raw;
+    *reinterpret_cast<__nv_bfloat162 *>(&raw.x) = __floats2bfloat162_rn(v.x, v.y);
+    *reinterpret_cast<__nv_bfloat162 *>(&raw.y) = __floats2bfloat162_rn(v.z, v.w);
+    *reinterpret_cast<uint2 *>(p) = raw;
+}
+__device__ __forceinline__ float4 load4(const __half *p)
+{
+    const uint2 raw = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void store4(__half *p, float4 v)
+{
+    uint2 raw;
+    *reinterpret_cast<__half2 *>(&raw.x) = __floats2half2_rn(v.x, v.y);
+    *reinterpret_cast<__half2 *>(&raw.y) = __floats2half2_rn(v.z, v.w);
+    *reinterpret_cast<uint2 *>(p) = raw;
+}
+
+// r -= alpha q, with q stored as kappa q: r -= (alpha / kappa) q_stored. FP32 arithmetic,
+// r and q in the storage type T (both buffers 256-byte aligned).
+template <typename T>
+__global__ void k_update_r(T *__restrict__ r, const T *__restrict__ q, const Scalars *sc, size_t n)
+{
+    const float a = (float)(sc->alpha / sc->kappa);
     const size_t n4 = n / 4;
-    float4 *r4 = reinterpret_cast<float4 *>(r);
-    const float4 *q4 = reinterpret_cast<const float4 *>(q);
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
-        float4 rv = r4[i];
-        const float4 qv = q4[i];
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        float4 rv = load4(r + 4 * i);
+        const float4 qv = load4(q + 4 * i);
         rv.x = fmaf(-a, qv.x, rv.x);
         rv.y = fmaf(-a, qv.y, rv.y);
         rv.z = fmaf(-a, qv.z, rv.z);
         rv.w = fmaf(-a, qv.w, rv.w);
-        r4[i] = rv;
+        store4(r + 4 * i, rv);
     }
-    for (size_t i = 4 * n4 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        r[i] = fmaf(-a, q[i], r[i]);
+    for (size_t i = 4 * n4 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float rv = fmaf(-a, load_as_float(q + i), load_as_float(r + i));
+        store_from_float(r + i, rv);
+    }
+}
+
+static cbct_status launch_update_r(void *r, const void *q, const Scalars *sc, size_t n, int storage, cudaStream_t st)
+{
+    if (storage == ST_BF16)
+        CBCT_TIMED(CBCT_KERNEL_OTHER, st,
+                   k_update_r<<<vec_blocks(n), 256, 0, st>>>(static_cast<__nv_bfloat16 *>(r),
+                                                             static_cast<const __nv_bfloat16 *>(q), sc, n));
+    else if (storage == ST_F16)
+        CBCT_TIMED(CBCT_KERNEL_OTHER, st,
+                   k_update_r<<<vec_blocks(n), 256, 0, st>>>(static_cast<__half *>(r), static_cast<const __half *>(q),
+                                                             sc, n));
+    else
+        CBCT_TIMED(CBCT_KERNEL_OTHER, st,
+                   k_update_r<<<vec_blocks(n), 256, 0, st>>>(static_cast<float *>(r), static_cast<const float *>(q), sc, n));
+    return check_cuda(cudaGetLastError(), "update launch");
 }
 
 // x += alpha p; and if with_p: p = s + beta p
@@ -278,7 +330,8 @@ static cbct_status launch_prolong(const Grid3 &cg, const float *fc, const Grid3 
 // ------------------------------------------------------------------------------------
 
 struct Work {
-    float *X, *X2, *P, *S, *Fa, *Fb, *R, *Q; // X, X2: the CGLS iterate and the next momentum point
+    float *X, *X2, *P, *S, *Fa, *Fb; // X, X2: the CGLS iterate and the next momentum point
+    void *R, *Q; // residual and projected search direction: n_views*nv*nu values of the storage type
     float2 *PS; // row prefix sums of the prescaled residual, input of the adjoint
     double *partials;
     Scalars *sc;
@@ -309,7 +362,7 @@ static size_t work_layout(const cbct_geometry *g, char *base, Work *w)
     };
     float *X = (float *)take(4 * N), *X2 = (float *)take(4 * N), *P = (float *)take(4 * N), *S = (float *)take(4 * N);
     float *Fa = (float *)take(4 * N), *Fb = (float *)take(4 * N);
-    float *R = (float *)take(4 * M), *Q = (float *)take(4 * M);
+    void *R = take(4 * M), *Q = take(4 * M); // sized for FP32, the widest storage type
     float2 *PS = (float2 *)take(sizeof(float2) * prefix_elems(d));
     double *partials = (double *)take(sizeof(double) * max_partials(g));
     Scalars *sc = (Scalars *)take(sizeof(Scalars));
@@ -352,33 +405,36 @@ static cbct_status get_work(cbct_geometry *g, void *ws, size_t ws_bytes, Work *w
         if (_s != CBCT_OK) return _s;                                                              \
     } while (0)
 
-static cbct_status run_cgls(const GeomDev &G, const float *y, float *x, int n_iter, const Work &w,
+static cbct_status run_cgls(const GeomDev &G, const float *y, float *x, int n_iter, const Work &w, int storage,
                             cudaStream_t st)
 {
     const long long sz = 1, sx = G.nz, sy = (long long)G.nx * G.nz;
     const size_t N = (size_t)G.nx * G.ny * G.nz, M = (size_t)G.nviews * G.nv * G.nu;
     const int nbp = project_num_blocks(G), nbb = backproject_num_blocks(G);
-    // r = y - P x (stored as |D-S| r); s = P^T r; p = s; gamma = ||s||^2
-    TRY(launch_project(G, x, sx, sy, sz, y, w.R, PM_R_PRESCALED, w.partials, 0.0f, st));
+    // FP32 storage holds |D-S| r and |D-S| q; 16-bit storage holds r and kappa q and the
+    // row prefix applies |D-S|. Only FP16 needs kappa (BF16 has FP32's exponent range).
+    const int prescale = storage == ST_F32 ? 0 : 1;
+    const int scale_q = storage == ST_F16 ? 1 : 0;
+    // r = y - P x; s = P^T r; p = s; gamma = ||s||^2
+    TRY(launch_project(G, x, sx, sy, sz, y, w.R, PM_RESID, w.partials, 0.0f, st, storage, w.sc));
     TRY(finalize(w.partials, nbp, w.sc, FIN_RR, st));
-    TRY(launch_row_prefix(G, w.R, w.PS, 0, st));
+    TRY(launch_row_prefix(G, w.R, w.PS, prescale, st, storage));
     TRY(launch_backproject(G, w.PS, w.S, sx, sy, sz, w.P, w.partials, st));
-    TRY(finalize(w.partials, nbb, w.sc, FIN_GAMMA, st));
+    TRY(finalize(w.partials, nbb, w.sc, FIN_GAMMA, st, scale_q));
     for (int l = 0; l < n_iter; ++l) {
         // q = P p, alpha = gamma / ||q||^2
-        TRY(launch_project(G, w.P, sx, sy, sz, nullptr, w.Q, PM_Q_PRESCALED, w.partials, 0.0f, st));
+        TRY(launch_project(G, w.P, sx, sy, sz, nullptr, w.Q, PM_Q_SCALED, w.partials, 0.0f, st, storage, w.sc));
         TRY(finalize(w.partials, nbp, w.sc, FIN_ALPHA, st));
         if (l == n_iter - 1) { // last update: x only; s and p would not be used again
             CBCT_TIMED(CBCT_KERNEL_OTHER, st, k_update_xp<<<vec_blocks(N), 256, 0, st>>>(x, w.P, w.S, w.sc, N, 0));
             TRY(check_cuda(cudaGetLastError(), "update launch"));
             break;
         }
-        CBCT_TIMED(CBCT_KERNEL_OTHER, st, k_update_r<<<vec_blocks(M), 256, 0, st>>>(w.R, w.Q, w.sc, M));
-        TRY(check_cuda(cudaGetLastError(), "update launch"));
+        TRY(launch_update_r(w.R, w.Q, w.sc, M, storage, st));
         // s = P^T r, beta = ||s||^2 / gamma
-        TRY(launch_row_prefix(G, w.R, w.PS, 0, st));
+        TRY(launch_row_prefix(G, w.R, w.PS, prescale, st, storage));
         TRY(launch_backproject(G, w.PS, w.S, sx, sy, sz, nullptr, w.partials, st));
-        TRY(finalize(w.partials, nbb, w.sc, FIN_BETA, st));
+        TRY(finalize(w.partials, nbb, w.sc, FIN_BETA, st, scale_q));
         // x += alpha p; p = s + beta p
         CBCT_TIMED(CBCT_KERNEL_OTHER, st, k_update_xp<<<vec_blocks(N), 256, 0, st>>>(x, w.P, w.S, w.sc, N, 1));
         TRY(check_cuda(cudaGetLastError(), "update launch"));
@@ -413,7 +469,7 @@ static cbct_status run_a2(const GeomDev &G, const float *y, float mu, int iters,
     TRY(check_cuda(cudaMemcpyAsync(w.X, *f_cur, sizeof(float) * N, cudaMemcpyDeviceToDevice, st), "copy"));
     double t = 1.0; // t^(k)
     for (int k = 0; k < iters; ++k) {
-        TRY(run_cgls(G, y, w.X, o.n_cgls, w, st));
+        TRY(run_cgls(G, y, w.X, o.n_cgls, w, o.storage, st));
         // f^(k+1) = H(D^T T_mu D x) fused with the next momentum point
         // v^(k+1) = f^(k+1) + (t^(k) - 1) / t^(k+1) (f^(k+1) - f^(k)) into X2;
         // internal layout: axis 0 = z, axis 1 = x, axis 2 = y
@@ -475,10 +531,14 @@ static cbct_status check_geom(const cbct_geometry *g, const char *what)
     return CBCT_OK;
 }
 
-extern "C" cbct_status cbct_project(const cbct_geometry *gc, const float *f, float *g_out, cbct_stream_t stream)
+static bool valid_dtype(int t) { return t == CBCT_F32 || t == CBCT_BF16 || t == CBCT_F16; }
+
+extern "C" cbct_status cbct_project_ex(const cbct_geometry *gc, const float *f, void *g_out, cbct_dtype g_type,
+                                       cbct_stream_t stream)
 {
     TRY(check_geom(gc, "project"));
     if (!f || !g_out) return set_error(CBCT_ERR_INVALID_ARG, "project: null pointer");
+    if (!valid_dtype(g_type)) return set_error(CBCT_ERR_INVALID_ARG, "project: unknown storage type %d", (int)g_type);
     cbct_geometry *g = const_cast<cbct_geometry *>(gc);
     const GeomDev G = level_geom(g, 0);
     const size_t N = (size_t)G.nx * G.ny * G.nz;
@@ -486,39 +546,67 @@ extern "C" cbct_status cbct_project(const cbct_geometry *gc, const float *f, flo
     cudaStream_t st = (cudaStream_t)stream;
     float *fz = g->d_scratch;
     TRY(transpose(f, fz, G.nx, G.ny, G.nz, true, st));
-    return launch_project(G, fz, G.nz, (long long)G.nx * G.nz, 1, nullptr, g_out, PM_PLAIN, nullptr, 0.0f, st);
+    return launch_project(G, fz, G.nz, (long long)G.nx * G.nz, 1, nullptr, g_out, PM_PLAIN, nullptr, 0.0f, st,
+                          (int)g_type);
 }
 
-extern "C" cbct_status cbct_backproject(const cbct_geometry *gc, const float *gin, float *f, cbct_stream_t stream)
+extern "C" cbct_status cbct_project(const cbct_geometry *gc, const float *f, float *g_out, cbct_stream_t stream)
+{
+    return cbct_project_ex(gc, f, g_out, CBCT_F32, stream);
+}
+
+extern "C" cbct_status cbct_backproject_ex(const cbct_geometry *gc, const void *gin, cbct_dtype g_type, float *f,
+                                           cbct_stream_t stream)
 {
     TRY(check_geom(gc, "backproject"));
     if (!gin || !f) return set_error(CBCT_ERR_INVALID_ARG, "backproject: null pointer");
+    if (!valid_dtype(g_type)) return set_error(CBCT_ERR_INVALID_ARG, "backproject: unknown storage type %d", (int)g_type);
     cbct_geometry *g = const_cast<cbct_geometry *>(gc);
     const GeomDev G = level_geom(g, 0);
     TRY(ensure_scratch(g, sizeof(float2) * prefix_elems(g->desc)));
     cudaStream_t st = (cudaStream_t)stream;
     float2 *ps = reinterpret_cast<float2 *>(g->d_scratch);
-    TRY(launch_row_prefix(G, gin, ps, 1, st));
+    TRY(launch_row_prefix(G, gin, ps, 1, st, (int)g_type));
     return launch_backproject(G, ps, f, 1, G.nx, (long long)G.nx * G.ny, nullptr, nullptr, st);
 }
 
-extern "C" cbct_status cbct_tf_analyze(int nx, int ny, int nz, const float *f, float *alpha27, cbct_stream_t stream)
+extern "C" cbct_status cbct_backproject(const cbct_geometry *gc, const float *gin, float *f, cbct_stream_t stream)
+{
+    return cbct_backproject_ex(gc, gin, CBCT_F32, f, stream);
+}
+
+extern "C" cbct_status cbct_tf_analyze_ex(int nx, int ny, int nz, const float *f, void *alpha27, cbct_dtype a_type,
+                                          cbct_stream_t stream)
 {
     if (nx < 1 || ny < 1 || nz < 1) return set_error(CBCT_ERR_INVALID_ARG, "tf_analyze: sizes must be >= 1");
     if (ny > 65535 * 8) return set_error(CBCT_ERR_INVALID_ARG, "tf_analyze: ny too large");
     if (!f || !alpha27) return set_error(CBCT_ERR_INVALID_ARG, "tf_analyze: null pointer");
     if ((double)nx * ny * nz * 27.0 > 9.2e18) return set_error(CBCT_ERR_INVALID_ARG, "tf_analyze: too large");
-    return launch_tf_analyze(nx, ny, nz, f, alpha27, (cudaStream_t)stream);
+    if (!valid_dtype(a_type)) return set_error(CBCT_ERR_INVALID_ARG, "tf_analyze: unknown storage type %d", (int)a_type);
+    return launch_tf_analyze(nx, ny, nz, f, alpha27, (cudaStream_t)stream, (int)a_type);
 }
 
-extern "C" cbct_status cbct_tf_synthesize_shrink(int nx, int ny, int nz, const float *alpha27, float mu,
-                                                 int positivity, float *f, cbct_stream_t stream)
+extern "C" cbct_status cbct_tf_analyze(int nx, int ny, int nz, const float *f, float *alpha27, cbct_stream_t stream)
+{
+    return cbct_tf_analyze_ex(nx, ny, nz, f, alpha27, CBCT_F32, stream);
+}
+
+extern "C" cbct_status cbct_tf_synthesize_shrink_ex(int nx, int ny, int nz, const void *alpha27, cbct_dtype a_type,
+                                                    float mu, int positivity, float *f, cbct_stream_t stream)
 {
     if (nx < 1 || ny < 1 || nz < 1) return set_error(CBCT_ERR_INVALID_ARG, "tf_synthesize_shrink: sizes must be >= 1");
     if (ny > 65535 * 8) return set_error(CBCT_ERR_INVALID_ARG, "tf_synthesize_shrink: ny too large");
     if (!f || !alpha27) return set_error(CBCT_ERR_INVALID_ARG, "tf_synthesize_shrink: null pointer");
     if (!(mu >= 0.0f) || !std::isfinite(mu)) return set_error(CBCT_ERR_INVALID_ARG, "tf_synthesize_shrink: mu must be finite and >= 0");
-    return launch_tf_synth_shrink(nx, ny, nz, alpha27, mu, positivity, f, (cudaStream_t)stream);
+    if (!valid_dtype(a_type))
+        return set_error(CBCT_ERR_INVALID_ARG, "tf_synthesize_shrink: unknown storage type %d", (int)a_type);
+    return launch_tf_synth_shrink(nx, ny, nz, alpha27, mu, positivity, f, (cudaStream_t)stream, (int)a_type);
+}
+
+extern "C" cbct_status cbct_tf_synthesize_shrink(int nx, int ny, int nz, const float *alpha27, float mu,
+                                                 int positivity, float *f, cbct_stream_t stream)
+{
+    return cbct_tf_synthesize_shrink_ex(nx, ny, nz, alpha27, CBCT_F32, mu, positivity, f, stream);
 }
 
 extern "C" cbct_status cbct_reconstruct_workspace_size(const cbct_geometry *g, size_t *bytes)
@@ -541,6 +629,8 @@ static cbct_status validate_recon(const float *y, const cbct_geometry *g, float 
     for (int i = 0; i < levels; ++i)
         if (iters[i] < 0 || iters[i] > 100000) return set_error(CBCT_ERR_INVALID_ARG, "reconstruct: bad iteration count");
     if (o.n_cgls < 1 || o.n_cgls > 1000) return set_error(CBCT_ERR_INVALID_ARG, "reconstruct: n_cgls must be in 1..1000");
+    if (o.storage != CBCT_F32 && o.storage != CBCT_BF16 && o.storage != CBCT_F16)
+        return set_error(CBCT_ERR_INVALID_ARG, "reconstruct: storage must be CBCT_F32, CBCT_BF16 or CBCT_F16");
     return CBCT_OK;
 }
 
@@ -549,7 +639,7 @@ extern "C" cbct_status cbct_reconstruct_ex(const float *y, const cbct_geometry *
                                            void *workspace, size_t workspace_bytes, float *f_out,
                                            cbct_stream_t stream)
 {
-    cbct_recon_opts o{3, 1, 1};
+    cbct_recon_opts o{3, 1, 1, CBCT_F32};
     if (opts) o = *opts;
     TRY(validate_recon(y, g, mu, lambda, levels, iters, f_out, o));
     return reconstruct_impl(y, const_cast<cbct_geometry *>(g), mu, levels, iters, o, workspace, workspace_bytes,
@@ -574,7 +664,7 @@ extern "C" cbct_status cbct_cgls(const cbct_geometry *gc, const float *y, float 
     TRY(reset_scalars(w, st));
     const GeomDev G = level_geom(g, 0);
     TRY(transpose(x, w.Fa, G.nx, G.ny, G.nz, true, st));
-    if (n_iter > 0) TRY(run_cgls(G, y, w.Fa, n_iter, w, st));
+    if (n_iter > 0) TRY(run_cgls(G, y, w.Fa, n_iter, w, ST_F32, st));
     TRY(transpose(w.Fa, x, G.nx, G.ny, G.nz, false, st));
     return read_flags(w, st);
 }

@@ -52,8 +52,9 @@ static int tf_chunk(int n0, int n1, int n2)
     return (int)((n2 + nch - 1) / nch);
 }
 
+template <typename TA_T>
 __global__ void __launch_bounds__(TF_THREADS)
-k_tf_analyze(int n0, int n1, int n2, int chunk, const float *__restrict__ f, float *__restrict__ alpha)
+k_tf_analyze(int n0, int n1, int n2, int chunk, const float *__restrict__ f, TA_T *__restrict__ alpha)
 {
     __shared__ float s[3][TB + 2][TA + 2];
     const int a0 = blockIdx.x * TA, b0 = blockIdx.y * TB;
@@ -110,9 +111,9 @@ k_tf_analyze(int n0, int n1, int n2, int chunk, const float *__restrict__ f, flo
                 for (int l = 0; l < 3; ++l) {
                     float w0, w1, w2;
                     ana3(u[0][m][l], u[1][m][l], u[2][m][l], w0, w1, w2);
-                    __stcs(alpha + (size_t)(l + 3 * m) * N + o, w0);
-                    __stcs(alpha + (size_t)(l + 3 * m + 9) * N + o, w1);
-                    __stcs(alpha + (size_t)(l + 3 * m + 18) * N + o, w2);
+                    store_stream(alpha + (size_t)(l + 3 * m) * N + o, w0);
+                    store_stream(alpha + (size_t)(l + 3 * m + 9) * N + o, w1);
+                    store_stream(alpha + (size_t)(l + 3 * m + 18) * N + o, w2);
                 }
         }
         __syncthreads();
@@ -123,8 +124,9 @@ constexpr int SA_PLANE = (TB + 2) * (TA + 2); // one channel of the haloed tile
 constexpr int SU_PLANE = (TB + 2) * TA;
 constexpr size_t TF_SYN_SMEM = sizeof(float) * (27 * SA_PLANE + 9 * SU_PLANE);
 
+template <typename TA_T>
 __global__ void __launch_bounds__(TF_THREADS)
-k_tf_synth_shrink(int n0, int n1, int n2, int chunk, const float *__restrict__ alpha, float mu,
+k_tf_synth_shrink(int n0, int n1, int n2, int chunk, const TA_T *__restrict__ alpha, float mu,
                   int positivity, float *__restrict__ f)
 {
     extern __shared__ float sm[];
@@ -156,14 +158,14 @@ k_tf_synth_shrink(int n0, int n1, int n2, int chunk, const float *__restrict__ a
         const int cw = wrapi(cp, n2);
         // 1. coefficients of plane cp on the haloed tile (the in-plane offsets are fixed)
         {
-            const float *src = alpha + (size_t)cw * n1 * n0;
+            const TA_T *src = alpha + (size_t)cw * n1 * n0;
 #pragma unroll 1
             for (int k = 0; k < 2; ++k) {
                 if (off[k] >= 0) {
-                    const float *p = src + off[k];
+                    const TA_T *p = src + off[k];
                     float *d = sa + tid + k * TF_THREADS;
 #pragma unroll 9
-                    for (int ch = 0; ch < 27; ++ch) d[ch * SA_PLANE] = __ldg(p + (size_t)ch * N);
+                    for (int ch = 0; ch < 27; ++ch) d[ch * SA_PLANE] = load_as_float(p + (size_t)ch * N);
                 }
             }
         }
@@ -214,29 +216,44 @@ k_tf_synth_shrink(int n0, int n1, int n2, int chunk, const float *__restrict__ a
     }
 }
 
-cbct_status launch_tf_analyze(int n0, int n1, int n2, const float *f, float *alpha, cudaStream_t st)
+cbct_status launch_tf_analyze(int n0, int n1, int n2, const float *f, void *alpha, cudaStream_t st, int storage)
 {
     const int chunk = tf_chunk(n0, n1, n2);
     dim3 grid((n0 + TA - 1) / TA, (n1 + TB - 1) / TB, (n2 + chunk - 1) / chunk);
-    CBCT_TIMED(CBCT_KERNEL_TF_ANALYZE, st, k_tf_analyze<<<grid, dim3(TA, TB), 0, st>>>(n0, n1, n2, chunk, f, alpha));
+    if (storage == ST_BF16)
+        CBCT_TIMED(CBCT_KERNEL_TF_ANALYZE, st,
+                   k_tf_analyze<<<grid, dim3(TA, TB), 0, st>>>(n0, n1, n2, chunk, f, static_cast<__nv_bfloat16 *>(alpha)));
+    else if (storage == ST_F16)
+        CBCT_TIMED(CBCT_KERNEL_TF_ANALYZE, st,
+                   k_tf_analyze<<<grid, dim3(TA, TB), 0, st>>>(n0, n1, n2, chunk, f, static_cast<__half *>(alpha)));
+    else
+        CBCT_TIMED(CBCT_KERNEL_TF_ANALYZE, st,
+                   k_tf_analyze<<<grid, dim3(TA, TB), 0, st>>>(n0, n1, n2, chunk, f, static_cast<float *>(alpha)));
     return check_cuda(cudaGetLastError(), "tf_analyze launch");
 }
 
-cbct_status launch_tf_synth_shrink(int n0, int n1, int n2, const float *alpha, float mu,
-                                   int positivity, float *f, cudaStream_t st)
+template <typename TA_T>
+static cbct_status launch_tf_synth_shrink_t(int n0, int n1, int n2, const TA_T *alpha, float mu, int positivity,
+                                            float *f, cudaStream_t st)
 {
-    static bool attr_set = false; // per process; the attribute is per function
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tf_synth_shrink, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)TF_SYN_SMEM);
-        if (e != cudaSuccess) return check_cuda(e, "tf_synth_shrink attribute");
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> done{0};
+    cudaError_t e = smem_optin_once(k_tf_synth_shrink<TA_T>, (int)TF_SYN_SMEM, done);
+    if (e != cudaSuccess) return check_cuda(e, "tf_synth_shrink attribute");
     const int chunk = tf_chunk(n0, n1, n2);
     dim3 grid((n0 + TA - 1) / TA, (n1 + TB - 1) / TB, (n2 + chunk - 1) / chunk);
     CBCT_TIMED(CBCT_KERNEL_TF_SYNTH, st,
-               k_tf_synth_shrink<<<grid, dim3(TA, TB), TF_SYN_SMEM, st>>>(n0, n1, n2, chunk, alpha, mu, positivity, f));
+               k_tf_synth_shrink<TA_T><<<grid, dim3(TA, TB), TF_SYN_SMEM, st>>>(n0, n1, n2, chunk, alpha, mu, positivity, f));
     return check_cuda(cudaGetLastError(), "tf_synth_shrink launch");
+}
+
+cbct_status launch_tf_synth_shrink(int n0, int n1, int n2, const void *alpha, float mu,
+                                   int positivity, float *f, cudaStream_t st, int storage)
+{
+    if (storage == ST_BF16)
+        return launch_tf_synth_shrink_t(n0, n1, n2, static_cast<const __nv_bfloat16 *>(alpha), mu, positivity, f, st);
+    if (storage == ST_F16)
+        return launch_tf_synth_shrink_t(n0, n1, n2, static_cast<const __half *>(alpha), mu, positivity, f, st);
+    return launch_tf_synth_shrink_t(n0, n1, n2, static_cast<const float *>(alpha), mu, positivity, f, st);
 }
 
 } // namespace cbct
@@ -376,13 +393,9 @@ k_tf_shrink_fused(int n0, int n1, int n2, int chunk, const float *__restrict__ x
 cbct_status launch_tf_shrink_fused(int n0, int n1, int n2, const float *x, float mu, int positivity, float *fnew,
                                    const float *fold, float coef, float *vout, cudaStream_t st)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tf_shrink_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)TF_FUSED_SMEM);
-        if (e != cudaSuccess) return check_cuda(e, "tf_shrink_fused attribute");
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> done{0};
+    cudaError_t e = smem_optin_once(k_tf_shrink_fused, (int)TF_FUSED_SMEM, done);
+    if (e != cudaSuccess) return check_cuda(e, "tf_shrink_fused attribute");
     const int chunk = tf_chunk(n0, n1, n2);
     dim3 grid((n0 + TA - 1) / TA, (n1 + TB - 1) / TB, (n2 + chunk - 1) / chunk);
     CBCT_TIMED(CBCT_KERNEL_TF_SYNTH, st,

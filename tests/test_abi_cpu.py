@@ -72,3 +72,13 @@ def test_null_arguments_are_rejected(lib):
     it = (ctypes.c_int * 1)(1)
     assert lib.cbct_reconstruct(None, None, 1e-3, 0.0, 1, it, None, None) == 1
     assert lib.cbct_geometry_destroy(None) == 0
+
+
+def test_typed_entry_points_reject_bad_arguments_before_device_work(lib):
+    p = ctypes.c_void_p(16)
+    assert lib.cbct_tf_analyze_ex(4, 4, 4, p, p, 3, None) == 1            # unknown storage type
+    assert lib.cbct_tf_analyze_ex(4, 4, 4, None, p, 1, None) == 1         # null input
+    assert lib.cbct_tf_synthesize_shrink_ex(4, 4, 4, p, -1, 1e-3, 1, p, None) == 1
+    assert lib.cbct_tf_synthesize_shrink_ex(4, 4, 4, p, 2, float("nan"), 1, p, None) == 1
+    assert lib.cbct_project_ex(None, p, p, 1, None) == 1
+    assert lib.cbct_backproject_ex(None, p, 2, p, None) == 1
