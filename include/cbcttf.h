@@ -49,7 +49,8 @@ typedef enum {
     CBCT_ERR_OUT_OF_MEMORY = 2, /* device allocation failed, or the workspace is too small */
     CBCT_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
     CBCT_ERR_NONFINITE = 4,     /* an inner product of the iteration was NaN or Inf */
-    CBCT_ERR_UNSUPPORTED = 5    /* a parameter the method does not define (e.g. lambda != 0) */
+    CBCT_ERR_UNSUPPORTED = 5,   /* a parameter the method does not define (e.g. lambda != 0) */
+    CBCT_ERR_TIMEOUT = 6        /* a wait ended before the awaited work finished */
 } cbct_status;
 
 /* Scan geometry (Section 2.1, Fig. 1; Section 3 gives sad = 1000 mm, sdd = 1500 mm). */
@@ -285,6 +286,95 @@ cbct_status cbct_count_nnz(const cbct_geometry *geom, int level, unsigned long l
 #define CBCT_PROJECT_STATIC_MAX_VOXELS 4194304
 cbct_status cbct_project_static(const cbct_geometry *geom, const float *f, float *g,
                                 cbct_stream_t stream);
+
+/*
+ * Request server: reconstructions of different geometries, view counts, noise levels and
+ * storage types served concurrently on one GPU (continuous batching). The paper
+ * reconstructs one scan at a time; this is an execution interface around the same
+ * reconstruction, not a step of the method.
+ *
+ * Each submitted request is a full cbct_reconstruct_ex call described by its geometry,
+ * host projections and options. A worker thread owned by the server admits queued
+ * requests whenever a stream slot is free and the device bytes of all admitted requests
+ * stay within the budget (granted in submission order); requests submitted while others
+ * run are admitted as soon as slots and memory free up, and their kernels overlap on the
+ * device. Two rules keep overlap from costing throughput: the summed volumes of the
+ * admitted requests stay within an L2 bound (a request that would break it waits, and
+ * smaller requests behind it may start first for a bounded time), and smaller requests
+ * run on higher-priority streams.
+ * An admitted request holds one device block (its geometry tables, y, the reconstruction
+ * workspace and the output volume) taken from a stream-ordered memory pool; it runs on
+ * its slot's stream as: copy y in, the whole multigrid iteration (captured once into a
+ * CUDA graph and launched, when use_graphs != 0), copy the volume out. The block returns
+ * to the pool when the request completes. The result of a request does not depend on
+ * what else runs: every kernel of the iteration is deterministic and requests share no
+ * device state.
+ */
+typedef struct cbct_server cbct_server;
+
+typedef struct {
+    size_t hbm_budget_bytes; /* device bytes admitted requests may hold together; 0 = 150 GB,
+                                capped at 90% of the device memory free at creation */
+    int max_active;          /* requests on the device at once (one stream each), 1..64 */
+    int use_graphs;          /* 1 = capture each request's iteration into a CUDA graph */
+    size_t l2_budget_bytes;  /* bound on the summed finest-volume bytes of the admitted
+                                requests, so that the volumes the projectors re-read stay in
+                                L2 together (an idle device always admits); 0 = the device's
+                                L2 size */
+    int size_priority;       /* 1 = requests get stream priority by volume size, smallest
+                                first (their thread blocks are scheduled ahead) */
+    double max_bypass_s;     /* a queued request held back by the L2 bound is overtaken by
+                                later requests only until it has waited this long; 0 = 2 s */
+} cbct_server_opts;
+
+/* Times are seconds on a steady clock since the server was created. */
+typedef struct {
+    int status;             /* cbct_status of the request (OK once complete) */
+    int done;               /* 1 when the volume has been written to f_host */
+    double t_submit;        /* cbct_server_submit returned */
+    double t_admit;         /* the worker admitted the request (device block taken) */
+    double t_done;          /* the worker saw the request's work complete */
+    size_t device_bytes;    /* size of the request's device block */
+} cbct_request_info;
+
+typedef struct {
+    long long submitted, completed, failed;
+    int queued, active, max_active_seen;
+    size_t bytes_in_use, max_bytes_seen, budget_bytes, l2_budget_bytes;
+    long long bypassed;      /* admissions that overtook an earlier queued request */
+} cbct_server_stats;
+
+/*
+ * Creates a server on the current CUDA device (opts NULL = defaults: 150 GB budget,
+ * 16 slots, graphs on) and starts its worker thread. Errors: INVALID_ARG, CUDA.
+ */
+cbct_status cbct_server_create(const cbct_server_opts *opts, cbct_server **out);
+
+/*
+ * Queues a reconstruction (arguments and result as cbct_reconstruct_ex, with host
+ * buffers): y_host [n_views][nv][nu] and f_host [nz][ny][nx] must be page-locked host
+ * memory (cudaHostAlloc / cudaHostRegister) that stays valid and untouched until the
+ * request is done. desc->angles is copied. Returns at once with the request's id.
+ * Errors (nothing is queued): INVALID_ARG for bad arguments, pageable host buffers, or a
+ * request whose device block exceeds the whole budget; UNSUPPORTED as cbct_reconstruct.
+ */
+cbct_status cbct_server_submit(cbct_server *srv, const cbct_geometry_desc *desc, const float *y_host,
+                               float mu, float lambda, int levels, const int *iters,
+                               const cbct_recon_opts *opts, float *f_host, long long *id);
+
+/*
+ * Waits up to timeout_s seconds (< 0: without limit) for request `id`; fills info (may be
+ * NULL). Returns the request's own status once it is done (OUT_OF_MEMORY, CUDA or
+ * NONFINITE for a failed request, with the message in cbct_last_error), TIMEOUT if it is
+ * still queued or running, INVALID_ARG for an unknown id.
+ */
+cbct_status cbct_server_wait(cbct_server *srv, long long id, double timeout_s, cbct_request_info *info);
+
+/* Counters of the server (a snapshot). */
+cbct_status cbct_server_stats_get(cbct_server *srv, cbct_server_stats *stats);
+
+/* Finishes every queued and admitted request, stops the worker and frees the server. */
+cbct_status cbct_server_destroy(cbct_server *srv);
 
 /* Kernel families reported by cbct_kernel_time. */
 typedef enum {

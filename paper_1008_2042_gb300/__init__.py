@@ -94,6 +94,12 @@ _SIGNATURES = {
     "cbct_prolong": [_i, _i, _i, _d, _d, _d, _vp, _i, _i, _i, _d, _d, _d, _vp, _vp],
     "cbct_restrict": [_i, _i, _i, _d, _d, _d, _vp, _i, _i, _i, _d, _d, _d, _vp, _vp],
     "cbct_count_nnz": [_vp, _i, ctypes.POINTER(ctypes.c_ulonglong), _vp],
+    "cbct_server_create": [ctypes.c_void_p, ctypes.POINTER(_vp)],
+    "cbct_server_submit": [_vp, ctypes.POINTER(GeometryDesc), _vp, _f, _f, _i, ctypes.POINTER(_i),
+                           ctypes.POINTER(ReconOpts), _vp, ctypes.POINTER(ctypes.c_longlong)],
+    "cbct_server_wait": [_vp, ctypes.c_longlong, _d, _vp],
+    "cbct_server_stats_get": [_vp, _vp],
+    "cbct_server_destroy": [_vp],
     "cbct_profiling_enable": [_i],
     "cbct_profiling_reset": [],
     "cbct_kernel_time": [_i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_ulonglong)],
@@ -155,6 +161,24 @@ def version() -> str:
     return load_library().cbct_version().decode()
 
 
+def make_desc(desc=None, **kw):
+    """A GeometryDesc from any object with the fields of cbct_geometry_desc (nx, ny, nz,
+    dx, dy, dz, nu, nv, du, dv, n_views and optionally u_off, v_off, sad, sdd, angles), or
+    from keyword arguments. Returns (desc, angle array to keep alive while desc is used)."""
+    get = (lambda k, d=None: getattr(desc, k, d)) if desc is not None else (lambda k, d=None: kw.get(k, d))
+    n_views = int(get("n_views"))
+    angles = get("angles", None)
+    keep, ap = None, None
+    if angles is not None:
+        keep = (ctypes.c_double * n_views)(*[float(a) for a in angles])
+        ap = ctypes.cast(keep, ctypes.POINTER(ctypes.c_double))
+    d = GeometryDesc(int(get("nx")), int(get("ny")), int(get("nz")), float(get("dx")), float(get("dy")),
+                     float(get("dz")), int(get("nu")), int(get("nv")), float(get("du")), float(get("dv")),
+                     float(get("u_off", 0.0)), float(get("v_off", 0.0)), float(get("sad", 1000.0)),
+                     float(get("sdd", 1500.0)), n_views, ap)
+    return d, keep
+
+
 class Geometry:
     """Owns a cbct_geometry handle. Accepts any object with the fields of
     cbct_geometry_desc (nx, ny, nz, dx, dy, dz, nu, nv, du, dv, sad, sdd, n_views, and
@@ -162,23 +186,14 @@ class Geometry:
 
     def __init__(self, desc=None, **kw):
         lib = load_library()
-        get = (lambda k, d=None: getattr(desc, k, d)) if desc is not None else (lambda k, d=None: kw.get(k, d))
-        self.nx, self.ny, self.nz = int(get("nx")), int(get("ny")), int(get("nz"))
-        self.dx, self.dy, self.dz = float(get("dx")), float(get("dy")), float(get("dz"))
-        self.nu, self.nv = int(get("nu")), int(get("nv"))
-        self.du, self.dv = float(get("du")), float(get("dv"))
-        self.u_off, self.v_off = float(get("u_off", 0.0)), float(get("v_off", 0.0))
-        self.sad, self.sdd = float(get("sad", 1000.0)), float(get("sdd", 1500.0))
-        self.n_views = int(get("n_views"))
-        angles = get("angles", None)
-        self._angles = None
-        ap = None
-        if angles is not None:
-            self._angles = (ctypes.c_double * self.n_views)(*[float(a) for a in angles])
-            ap = ctypes.cast(self._angles, ctypes.POINTER(ctypes.c_double))
-        d = GeometryDesc(self.nx, self.ny, self.nz, self.dx, self.dy, self.dz, self.nu, self.nv,
-                         self.du, self.dv, self.u_off, self.v_off, self.sad, self.sdd,
-                         self.n_views, ap)
+        d, self._angles = make_desc(desc, **kw)
+        self.nx, self.ny, self.nz = d.nx, d.ny, d.nz
+        self.dx, self.dy, self.dz = d.dx, d.dy, d.dz
+        self.nu, self.nv = d.nu, d.nv
+        self.du, self.dv = d.du, d.dv
+        self.u_off, self.v_off = d.u_off, d.v_off
+        self.sad, self.sdd = d.sad, d.sdd
+        self.n_views = d.n_views
         h = ctypes.c_void_p()
         _check(lib.cbct_geometry_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
@@ -415,3 +430,102 @@ def kernel_times() -> dict:
         _check(lib.cbct_kernel_time(kind, ctypes.byref(ms), ctypes.byref(n)))
         out[name] = (float(ms.value), int(n.value))
     return out
+
+
+# ---------------------------------------------------------------------------------------
+# Request server (cbct_server_*): continuous batching of whole reconstructions
+# ---------------------------------------------------------------------------------------
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("l2_budget_bytes", ctypes.c_size_t), ("size_priority", ctypes.c_int),
+                ("max_bypass_s", ctypes.c_double)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("done", ctypes.c_int), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("queued", ctypes.c_int), ("active", ctypes.c_int), ("max_active_seen", ctypes.c_int),
+                ("bytes_in_use", ctypes.c_size_t), ("max_bytes_seen", ctypes.c_size_t),
+                ("budget_bytes", ctypes.c_size_t), ("l2_budget_bytes", ctypes.c_size_t),
+                ("bypassed", ctypes.c_longlong)]
+
+
+def _host(t: torch.Tensor, numel: int, name: str) -> ctypes.c_void_p:
+    if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 CPU tensor")
+    if not t.is_pinned():
+        raise TypeError(f"{name} must be in page-locked memory (tensor.pin_memory())")
+    if t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} values, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Server:
+    """A cbct_server on the current device: submit() queues a reconstruction with pinned
+    host buffers and returns at once; wait() blocks until it is done. Requests run
+    concurrently on the GPU, admitted by slots and by the device-memory budget."""
+
+    def __init__(self, budget_bytes: int = 0, max_active: int = 16, use_graphs: bool = True,
+                 l2_budget_bytes: int = 0, size_priority: bool = True, max_bypass_s: float = 0.0):
+        lib = load_library()
+        o = ServerOpts(int(budget_bytes), int(max_active), int(bool(use_graphs)), int(l2_budget_bytes),
+                       int(bool(size_priority)), float(max_bypass_s))
+        h = ctypes.c_void_p()
+        _check(lib.cbct_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}  # id -> host tensors that must outlive the request
+
+    def submit(self, geom, y_host: torch.Tensor, mu: float, levels: int, iters: Sequence[int],
+               out: torch.Tensor, lam: float = 0.0, n_cgls: int = 3, momentum: bool = True,
+               positivity: bool = True, storage=torch.float32) -> int:
+        d, angles = make_desc(geom)
+        if len(iters) != levels:
+            raise ValueError("iters must have one entry per level")
+        it = (ctypes.c_int * levels)(*[int(v) for v in iters])
+        opts = ReconOpts(int(n_cgls), int(bool(momentum)), int(bool(positivity)), DTYPES[storage_dtype(storage)])
+        py = _host(y_host, d.n_views * d.nv * d.nu, "y_host")
+        pf = _host(out, d.nx * d.ny * d.nz, "out")
+        rid = ctypes.c_longlong()
+        _check(load_library().cbct_server_submit(self._h, ctypes.byref(d), py, float(mu), float(lam), int(levels),
+                                                 it, ctypes.byref(opts), pf, ctypes.byref(rid)))
+        self._keep[rid.value] = (y_host, out, angles)
+        return int(rid.value)
+
+    def wait(self, rid: int, timeout: Optional[float] = None) -> dict:
+        """Blocks until request rid is done (raises CbctError on failure or timeout)."""
+        info = RequestInfo()
+        st = load_library().cbct_server_wait(self._h, int(rid), -1.0 if timeout is None else float(timeout),
+                                             ctypes.byref(info))
+        if st != 6:  # a timed-out request keeps its buffers alive
+            self._keep.pop(int(rid), None)
+        _check(st)
+        return {"status": info.status, "t_submit": info.t_submit, "t_admit": info.t_admit, "t_done": info.t_done,
+                "device_bytes": int(info.device_bytes)}
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(load_library().cbct_server_stats_get(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(load_library().cbct_server_destroy(self._h))
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcbcttf.so")
-SOURCES = ["geometry.cu", "project.cu", "backproject.cu", "tf.cu", "recon.cu", "project_static.cu"]
+SOURCES = ["geometry.cu", "project.cu", "backproject.cu", "tf.cu", "recon.cu", "project_static.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -229,4 +229,26 @@ struct cbct_geometry {
 namespace cbct {
 GeomDev level_geom(const cbct_geometry *g, int level);
 cbct_status ensure_scratch(cbct_geometry *g, size_t bytes);
+
+// Geometry pieces for callers that build a cbct_geometry in memory they own (the request
+// server): argument checks, the host view table (angles and FP32 cos/sin), and the
+// stream-ordered ray-table kernel.
+cbct_status validate_geometry_desc(const cbct_geometry_desc &d);
+void view_table(const cbct_geometry_desc &d, double *angles, float2 *cs);
+cbct_status launch_ray_table(const cbct_geometry *g, cudaStream_t st);
+
+// The reconstruction as pure stream work: no allocation, no synchronisation, nothing read
+// back (capturable into a CUDA graph). ws must hold reconstruct_ws_bytes(g) bytes, 256-byte
+// aligned; the iteration's status word (bit 0: a non-finite inner product) is at
+// reconstruct_flags_address(g, ws) once the work has run.
+cbct_status validate_recon_args(float mu, float lambda, int levels, const int *iters, const cbct_recon_opts &o);
+size_t reconstruct_ws_bytes(const cbct_geometry *g);
+cbct_status reconstruct_enqueue(const float *y, cbct_geometry *g, float mu, int levels, const int *iters,
+                                const cbct_recon_opts &o, void *ws, size_t ws_bytes, float *f_out, cudaStream_t st);
+const unsigned int *reconstruct_flags_address(const cbct_geometry *g, void *ws);
+
+// Sets every kernel attribute the launchers would otherwise set on first use (shared
+// memory opt-ins) on the current device, so that later launches can be graph-captured.
+cbct_status project_prepare();
+cbct_status tf_prepare();
 }

@@ -51,6 +51,9 @@ ProfToken prof_start(int kind, cudaStream_t st)
 {
     ProfToken t{nullptr, kind};
     if (!g_prof_on.load(std::memory_order_relaxed)) return t;
+    // work captured into a CUDA graph is not timed launch by launch
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return t;
     if (cudaEventCreate(&t.start) != cudaSuccess) {
         t.start = nullptr;
         return t;
@@ -207,12 +210,10 @@ extern "C" cbct_status cbct_kernel_time(int kind, double *total_ms, unsigned lon
     return st;
 }
 
-extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct_geometry **out)
+namespace cbct {
+
+cbct_status validate_geometry_desc(const cbct_geometry_desc &d)
 {
-    g_last_error[0] = '\0';
-    if (!desc || !out) return set_error(CBCT_ERR_INVALID_ARG, "geometry_create: null argument");
-    *out = nullptr;
-    const cbct_geometry_desc &d = *desc;
     if (d.nx < 1 || d.ny < 1 || d.nz < 1 || d.nu < 1 || d.nv < 1 || d.n_views < 1)
         return set_error(CBCT_ERR_INVALID_ARG, "geometry_create: sizes must be >= 1");
     if (d.nv > 8192) return set_error(CBCT_ERR_INVALID_ARG, "geometry_create: nv > 8192");
@@ -237,6 +238,40 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct
             if (!std::isfinite(d.angles[k]))
                 return set_error(CBCT_ERR_INVALID_ARG, "geometry_create: non-finite angle");
 
+    return CBCT_OK;
+}
+
+void view_table(const cbct_geometry_desc &d, double *angles, float2 *cs)
+{
+    for (int k = 0; k < d.n_views; k++) {
+        double t = d.angles ? d.angles[k] : 2.0 * M_PI * k / d.n_views;
+        angles[k] = t;
+        cs[k] = make_float2((float)std::cos(t), (float)std::sin(t));
+    }
+}
+
+cbct_status launch_ray_table(const cbct_geometry *g, cudaStream_t st)
+{
+    const size_t nrays = (size_t)g->desc.n_views * g->desc.nu;
+    const GeomDev G = level_geom(g, 0);
+    k_ray_table<<<(unsigned)((nrays + 127) / 128), 128, 0, st>>>(G, g->d_ray4, g->d_ray2);
+    note_launch();
+    return check_cuda(cudaGetLastError(), "ray table launch");
+}
+
+} // namespace cbct
+
+extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct_geometry **out)
+{
+    g_last_error[0] = '\0';
+    if (!desc || !out) return set_error(CBCT_ERR_INVALID_ARG, "geometry_create: null argument");
+    *out = nullptr;
+    const cbct_geometry_desc &d = *desc;
+    {
+        cbct_status v = validate_geometry_desc(d);
+        if (v != CBCT_OK) return v;
+    }
+
     cbct_geometry *g = (cbct_geometry *)calloc(1, sizeof(cbct_geometry));
     if (!g) return set_error(CBCT_ERR_OUT_OF_MEMORY, "geometry_create: host allocation");
     g->desc = d;
@@ -248,11 +283,7 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct
         free(g);
         return set_error(CBCT_ERR_OUT_OF_MEMORY, "geometry_create: host allocation");
     }
-    for (int k = 0; k < d.n_views; k++) {
-        double t = d.angles ? d.angles[k] : 2.0 * M_PI * k / d.n_views;
-        g->angles[k] = t;
-        h_cs[k] = make_float2((float)std::cos(t), (float)std::sin(t));
-    }
+    view_table(d, g->angles, h_cs);
     g->desc.angles = g->angles;
     cudaGetDevice(&g->device);
     const size_t nrays = (size_t)d.n_views * d.nu;

@@ -409,17 +409,43 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
     }
 }
 
+// per-device record of the shared-memory opt-in, one per kernel instantiation
+template <int MODE, typename TP> static std::atomic<unsigned long long> g_project_optin{0};
+
+template <int MODE, typename TP> static cbct_status project_optin()
+{
+    cudaError_t e = smem_optin_once(k_project<MODE, TP>, 200 * 1024, g_project_optin<MODE, TP>);
+    return e == cudaSuccess ? CBCT_OK : check_cuda(e, "project attribute");
+}
+
 template <int MODE, typename TP>
 static cbct_status launch_project_t(const GeomDev &G, const float *f, int isx, int isy, const float *y, void *out,
                                    double *partials, float count_thr, const Scalars *sc, dim3 grid, int threads,
                                    size_t smem, cudaStream_t st)
 {
-    static std::atomic<unsigned long long> done{0};
-    cudaError_t e = smem_optin_once(k_project<MODE, TP>, 200 * 1024, done);
-    if (e != cudaSuccess) return check_cuda(e, "project attribute");
+    {
+        cbct_status a = project_optin<MODE, TP>();
+        if (a != CBCT_OK) return a;
+    }
     k_project<MODE, TP><<<grid, threads, smem, st>>>(G, f, isx, isy, y, static_cast<TP *>(out),
                                                     partials, count_thr, sc);
     return CBCT_OK;
+}
+
+cbct_status project_prepare()
+{
+    cbct_status r = CBCT_OK;
+    if (r == CBCT_OK) r = project_optin<PM_PLAIN, float>();
+    if (r == CBCT_OK) r = project_optin<PM_PLAIN, __nv_bfloat16>();
+    if (r == CBCT_OK) r = project_optin<PM_PLAIN, __half>();
+    if (r == CBCT_OK) r = project_optin<PM_COUNT, float>();
+    if (r == CBCT_OK) r = project_optin<PM_Q_SCALED, float>();
+    if (r == CBCT_OK) r = project_optin<PM_Q_SCALED, __nv_bfloat16>();
+    if (r == CBCT_OK) r = project_optin<PM_Q_SCALED, __half>();
+    if (r == CBCT_OK) r = project_optin<PM_RESID, float>();
+    if (r == CBCT_OK) r = project_optin<PM_RESID, __nv_bfloat16>();
+    if (r == CBCT_OK) r = project_optin<PM_RESID, __half>();
+    return r;
 }
 
 cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long long sy,

@@ -489,9 +489,8 @@ static cbct_status run_a2(const GeomDev &G, const float *y, float mu, int iters,
     return CBCT_OK;
 }
 
-static cbct_status reconstruct_impl(const float *y, cbct_geometry *g, float mu, int levels, const int *iters,
-                                    const cbct_recon_opts &o, void *ws, size_t ws_bytes, float *f_out,
-                                    cudaStream_t st)
+cbct_status reconstruct_enqueue(const float *y, cbct_geometry *g, float mu, int levels, const int *iters,
+                                const cbct_recon_opts &o, void *ws, size_t ws_bytes, float *f_out, cudaStream_t st)
 {
     Work w;
     TRY(get_work(g, ws, ws_bytes, &w));
@@ -514,7 +513,25 @@ static cbct_status reconstruct_impl(const float *y, cbct_geometry *g, float mu, 
         Gprev = G;
     }
     const GeomDev G0 = level_geom(g, 0);
-    TRY(transpose(f_cur, f_out, G0.nx, G0.ny, G0.nz, false, st));
+    return transpose(f_cur, f_out, G0.nx, G0.ny, G0.nz, false, st);
+}
+
+size_t reconstruct_ws_bytes(const cbct_geometry *g) { return work_layout(g, nullptr, nullptr); }
+
+const unsigned int *reconstruct_flags_address(const cbct_geometry *g, void *ws)
+{
+    Work w;
+    work_layout(g, (char *)ws, &w);
+    return &w.sc->flags;
+}
+
+static cbct_status reconstruct_impl(const float *y, cbct_geometry *g, float mu, int levels, const int *iters,
+                                    const cbct_recon_opts &o, void *ws, size_t ws_bytes, float *f_out,
+                                    cudaStream_t st)
+{
+    TRY(reconstruct_enqueue(y, g, mu, levels, iters, o, ws, ws_bytes, f_out, st));
+    Work w;
+    TRY(get_work(g, ws, ws_bytes, &w));
     return read_flags(w, st);
 }
 
@@ -616,11 +633,10 @@ extern "C" cbct_status cbct_reconstruct_workspace_size(const cbct_geometry *g, s
     return CBCT_OK;
 }
 
-static cbct_status validate_recon(const float *y, const cbct_geometry *g, float mu, float lambda, int levels,
-                                  const int *iters, float *f_out, const cbct_recon_opts &o)
+namespace cbct {
+cbct_status validate_recon_args(float mu, float lambda, int levels, const int *iters, const cbct_recon_opts &o)
 {
-    TRY(check_geom(g, "reconstruct"));
-    if (!y || !f_out || !iters) return set_error(CBCT_ERR_INVALID_ARG, "reconstruct: null pointer");
+    if (!iters) return set_error(CBCT_ERR_INVALID_ARG, "reconstruct: null pointer");
     if (!(mu >= 0.0f) || !std::isfinite(mu)) return set_error(CBCT_ERR_INVALID_ARG, "reconstruct: mu must be finite and >= 0");
     if (!std::isfinite(lambda)) return set_error(CBCT_ERR_INVALID_ARG, "reconstruct: lambda must be finite");
     if (lambda != 0.0f)
@@ -632,6 +648,15 @@ static cbct_status validate_recon(const float *y, const cbct_geometry *g, float 
     if (o.storage != CBCT_F32 && o.storage != CBCT_BF16 && o.storage != CBCT_F16)
         return set_error(CBCT_ERR_INVALID_ARG, "reconstruct: storage must be CBCT_F32, CBCT_BF16 or CBCT_F16");
     return CBCT_OK;
+}
+} // namespace cbct
+
+static cbct_status validate_recon(const float *y, const cbct_geometry *g, float mu, float lambda, int levels,
+                                  const int *iters, float *f_out, const cbct_recon_opts &o)
+{
+    TRY(check_geom(g, "reconstruct"));
+    if (!y || !f_out || !iters) return set_error(CBCT_ERR_INVALID_ARG, "reconstruct: null pointer");
+    return validate_recon_args(mu, lambda, levels, iters, o);
 }
 
 extern "C" cbct_status cbct_reconstruct_ex(const float *y, const cbct_geometry *g, float mu, float lambda,

@@ -232,13 +232,22 @@ cbct_status launch_tf_analyze(int n0, int n1, int n2, const float *f, void *alph
     return check_cuda(cudaGetLastError(), "tf_analyze launch");
 }
 
+template <typename TA_T> static std::atomic<unsigned long long> g_synth_optin{0};
+
+template <typename TA_T> static cbct_status synth_optin()
+{
+    cudaError_t e = smem_optin_once(k_tf_synth_shrink<TA_T>, (int)TF_SYN_SMEM, g_synth_optin<TA_T>);
+    return e == cudaSuccess ? CBCT_OK : check_cuda(e, "tf_synth_shrink attribute");
+}
+
 template <typename TA_T>
 static cbct_status launch_tf_synth_shrink_t(int n0, int n1, int n2, const TA_T *alpha, float mu, int positivity,
                                             float *f, cudaStream_t st)
 {
-    static std::atomic<unsigned long long> done{0};
-    cudaError_t e = smem_optin_once(k_tf_synth_shrink<TA_T>, (int)TF_SYN_SMEM, done);
-    if (e != cudaSuccess) return check_cuda(e, "tf_synth_shrink attribute");
+    {
+        cbct_status a = synth_optin<TA_T>();
+        if (a != CBCT_OK) return a;
+    }
     const int chunk = tf_chunk(n0, n1, n2);
     dim3 grid((n0 + TA - 1) / TA, (n1 + TB - 1) / TB, (n2 + chunk - 1) / chunk);
     CBCT_TIMED(CBCT_KERNEL_TF_SYNTH, st,
@@ -390,12 +399,30 @@ k_tf_shrink_fused(int n0, int n1, int n2, int chunk, const float *__restrict__ x
     }
 }
 
+static std::atomic<unsigned long long> g_fused_optin{0};
+
+static cbct_status fused_optin()
+{
+    cudaError_t e = smem_optin_once(k_tf_shrink_fused, (int)TF_FUSED_SMEM, g_fused_optin);
+    return e == cudaSuccess ? CBCT_OK : check_cuda(e, "tf_shrink_fused attribute");
+}
+
+cbct_status tf_prepare()
+{
+    cbct_status r = synth_optin<float>();
+    if (r == CBCT_OK) r = synth_optin<__nv_bfloat16>();
+    if (r == CBCT_OK) r = synth_optin<__half>();
+    if (r == CBCT_OK) r = fused_optin();
+    return r;
+}
+
 cbct_status launch_tf_shrink_fused(int n0, int n1, int n2, const float *x, float mu, int positivity, float *fnew,
                                    const float *fold, float coef, float *vout, cudaStream_t st)
 {
-    static std::atomic<unsigned long long> done{0};
-    cudaError_t e = smem_optin_once(k_tf_shrink_fused, (int)TF_FUSED_SMEM, done);
-    if (e != cudaSuccess) return check_cuda(e, "tf_shrink_fused attribute");
+    {
+        cbct_status a = fused_optin();
+        if (a != CBCT_OK) return a;
+    }
     const int chunk = tf_chunk(n0, n1, n2);
     dim3 grid((n0 + TA - 1) / TA, (n1 + TB - 1) / TB, (n2 + chunk - 1) / chunk);
     CBCT_TIMED(CBCT_KERNEL_TF_SYNTH, st,
