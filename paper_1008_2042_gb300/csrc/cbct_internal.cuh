@@ -180,6 +180,11 @@ int device_sm_count();
 // Launchers (all asynchronous on `st`; return CBCT_ERR_CUDA on launch failure).
 // Volume element (ix, iy, iz) lives at ix*sx + iy*sy + iz*sz.
 int project_num_blocks(const GeomDev &G);
+// Bytes past the end of a volume that the projector may read (its 16-byte staging copies
+// round the last z-line up): every volume buffer passed to launch_project is allocated with
+// at least this much slack, and its base is 16-byte aligned.
+constexpr size_t PROJECT_VOLUME_SLACK = 64;
+
 // out holds `storage`-typed values (PM_COUNT: none); y is FP32; sc supplies kappa in
 // PM_Q_SCALED. With FP32 storage the CGLS modes store |D - S| r and |D - S| q.
 cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long long sy,

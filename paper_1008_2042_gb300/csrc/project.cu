@@ -20,6 +20,9 @@
 namespace cbct {
 
 constexpr int PROJ_THREADS = 192; // threads per block; each thread walks two imager rows
+#ifndef CBCT_PROJ_MIN_BLOCKS
+#define CBCT_PROJ_MIN_BLOCKS 4 // resident blocks per SM the register budget is sized for
+#endif
 constexpr float P_INF = 3.0e38f;
 
 // threads of a block (a multiple of 32, every lane present for warp votes) and the imager
@@ -37,8 +40,10 @@ int project_num_blocks(const GeomDev &G)
     return G.nviews * G.nu * ((G.nv + rows - 1) / rows);
 }
 
-// Number of column segments a lane processes per unrolled group.
-constexpr int SEG_GROUP = 16;
+// Column segments a lane processes per unrolled group: 32 where the geometry guarantees at
+// most one z-plane crossing per row in any 32 consecutive segments, else 16 (rows that
+// cross twice in a group take the exact sequential walk).
+constexpr int SEG_GROUP_MAX = 32;
 
 __device__ __forceinline__ int lower_count(const float *a, int n, float t) // # a[i] < t
 {
@@ -62,33 +67,48 @@ __device__ __forceinline__ int upper_count(const float *a, int n, float t) // # 
     return lo;
 }
 
-static inline int seg_capacity(const GeomDev &G)
+static inline int seg_capacity(const GeomDev &G, int sg)
 {
-    return ((G.nx + G.ny + 3 + SEG_GROUP - 1) / SEG_GROUP + 1) * SEG_GROUP;
+    return ((G.nx + G.ny + 3 + sg - 1) / sg + 1) * sg;
+}
+
+// The z distance a row covers over sg segments is at most (its z slope) x sg x (the voxel
+// column diagonal); the slope is |v| / (transverse source-pixel distance) <= max|v| / sdd.
+static inline int segment_group(const GeomDev &G)
+{
+    const double vmax = fmax(fabs((double)G.v_first), fabs((double)G.v_first + (G.nv - 1) * (double)G.dv));
+    const double diag = sqrt((double)G.dx * G.dx + (double)G.dy * G.dy);
+    return vmax / G.sdd * SEG_GROUP_MAX * diag < 0.95 * G.dz ? SEG_GROUP_MAX : SEG_GROUP_MAX / 2;
 }
 
 // Shared memory of one block: the two crossing lists, then (16-byte aligned) per segment
 // its end tau, its column offset and the packed record used by the walk.
 static inline int seg_offset(const GeomDev &G) { return ((G.nx + G.ny + 2 + 3) / 4) * 4; }
 
-// z-lines of one group of columns, staged in shared memory as adjacent-voxel pairs
-// (f[k], f[k+1]) indexed [k][column in group], the column pitch odd to spread banks.
-constexpr int LINE_PITCH = SEG_GROUP + 1;
+// z-lines of one group of columns, staged in shared memory one line per column. A column
+// starts at float offset col of the z-contiguous volume; its line is copied in 16-byte
+// pieces from col rounded down to a multiple of 4 up to col + nz rounded up, i.e. at most
+// nz + 6 floats, and the column's first voxel sits at (col & 3) in its line. The copy may
+// read up to 3 floats past the last voxel of the volume: every volume buffer the
+// projector reads has at least 16 bytes of slack after it (PROJECT_VOLUME_SLACK).
+static inline int line_pitch(int nz) { return ((nz + 6 + 3) / 4) * 4; }
 
-static inline int line_pairs(const GeomDev &G) { return G.nz > 1 ? G.nz - 1 : 1; }
-
-static inline size_t project_smem(const GeomDev &G)
+// shared memory: crossing lists, per segment (end tau, column offset, (line offset,
+// length)), two staged groups of z-lines and one group-sized line of zeros (read by rows
+// outside the volume)
+static inline size_t project_smem(const GeomDev &G, int sg)
 {
-    return sizeof(float) * (size_t)seg_offset(G) + (sizeof(float) + sizeof(int) + sizeof(float4)) * (size_t)seg_capacity(G) +
-           sizeof(float2) * 2 * (size_t)line_pairs(G) * LINE_PITCH;
+    return sizeof(float) * (size_t)seg_offset(G) + (sizeof(float) + sizeof(int) + sizeof(float2)) * (size_t)seg_capacity(G, sg) +
+           sizeof(float) * 3 * (size_t)sg * line_pitch(G.nz);
 }
 
-size_t project_smem_bytes(const GeomDev &G) { return project_smem(G); }
+size_t project_smem_bytes(const GeomDev &G) { return project_smem(G, segment_group(G)); }
 
-__device__ __forceinline__ void cp_async4(float *smem_dst, const float *gsrc)
+// 16-byte asynchronous global -> shared copy (L2 only); both addresses 16-byte aligned
+__device__ __forceinline__ void cp_async16(float *smem_dst, const float *gsrc)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -100,26 +120,28 @@ template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile(
 // of the other family before it (binary search); this yields the list of (x, y) voxel
 // columns the rays visit and the tau at which each is left. For every segment the block
 // also stores its length, 1 / length and its start relative to its group.
-// Phase 2 (one lane per imager row): walk the list in groups of SEG_GROUP columns. In a
+// Phase 2 (one lane per imager row): walk the list in groups of SG columns. In a
 // group a lane crosses at most one z plane (else an exact sequential walk is used): it
 // reads the voxel pair (kb, kb + 1) around its current and next slab in every column and
 // splits each column's length at its crossing with a saturated FMA. No branch and no
 // integer or compare instruction is spent per column.
-template <int MODE, typename TP>
-__global__ void __launch_bounds__(PROJ_THREADS, 4)
+template <int MODE, typename TP, int SG>
+__global__ void __launch_bounds__(PROJ_THREADS, CBCT_PROJ_MIN_BLOCKS)
 k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *__restrict__ y,
           TP *__restrict__ out, double *__restrict__ partials, float count_thr, const Scalars *__restrict__ sc)
 {
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) float smem[];
     __shared__ double s_warp[PROJ_THREADS / 32];
     float *sA = smem;                      // x-plane crossings, in ray order
     float *sB = sA + (G.nx + 1);           // y-plane crossings
-    const int cap = ((G.nx + G.ny + 3 + SEG_GROUP - 1) / SEG_GROUP + 1) * SEG_GROUP;
+    const int cap = ((G.nx + G.ny + 3 + SG - 1) / SG + 1) * SG;
     float *sEnd = smem + ((G.nx + G.ny + 2 + 3) / 4) * 4; // tau at which segment j ends
     int *sCol = reinterpret_cast<int *>(sEnd + cap);      // voxel-column offset of segment j
-    float4 *sSeg = reinterpret_cast<float4 *>(sCol + cap); // (column bits, length, 1/length, start term)
-    float2 *sPair = reinterpret_cast<float2 *>(sSeg + cap); // two staged groups of z-line pairs
-    const int npair = G.nz > 1 ? G.nz - 1 : 1;
+    float2 *sSeg = reinterpret_cast<float2 *>(sCol + cap); // (line offset bits, length) of segment j
+    const int pitch = ((G.nz + 6 + 3) / 4) * 4;            // floats per staged line
+    const int quads = pitch / 4;                           // 16-byte pieces per line slot
+    float *sLine = reinterpret_cast<float *>(sSeg + cap);  // two staged groups of z-lines
+    float *sZero = sLine + 2 * SG * pitch;                 // zeros, as long as one group
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int view = blockIdx.x / G.nu;
@@ -197,14 +219,12 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
     }
     __syncthreads();
     for (int q = tid; q < cap; q += nthr) {
-        const float e = sEnd[q];
         const float st = q ? sEnd[q - 1] : tau_in;
-        const int qg = q - q % SEG_GROUP;
-        const float g0 = qg ? sEnd[qg - 1] : tau_in; // start of q's group
-        const float len = e - st;
-        const float ia = len > 0.0f ? __frcp_rn(len) : 0.0f;
-        sSeg[q] = make_float4(__int_as_float(sCol[q]), len, ia, -(st - g0) * ia);
+        // where the column's first voxel lands in its staged line
+        const int loff = (q % SG) * pitch + (sCol[q] & 3);
+        sSeg[q] = make_float2(__int_as_float(loff), sEnd[q] - st);
     }
+    for (int q = tid; q < SG * pitch; q += nthr) sZero[q] = 0.0f;
     __syncthreads();
 
     // ---- phase 2: per-row z state (two rows per thread: iv[0] and iv[1] = iv[0] + nthr) ----
@@ -253,23 +273,23 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
         }
     } else if (hit) {
         // Stage the z-lines of each group of columns into shared memory one group ahead
-        // (cp.async), then let every row read its voxel pair there.
-        const int nchunk = (nseg + SEG_GROUP - 1) / SEG_GROUP;
-        const int line_elems = SEG_GROUP * G.nz;
-        const int u0 = tid / G.nz, k0 = tid - u0 * G.nz;
-        const int du = nthr / G.nz, dk = nthr - du * G.nz;
+        // (16-byte cp.async), then let every row read its voxel pair there.
+        const int nchunk = (nseg + SG - 1) / SG;
+        // 16-byte pieces of a group's lines: slot c = (line u, piece i), c = u * quads + i;
+        // thread tid takes c = tid, tid + nthr, ... (the same slots for every group)
+        const int u_0 = tid / quads, i_0 = tid - u_0 * quads;
+        const int du = nthr / quads, di = nthr - du * quads;
         auto fill = [&](int chunk, int buf) {
-            float2 *dst = sPair + buf * npair * LINE_PITCH;
-            const float4 *seg = sSeg + chunk * SEG_GROUP;
-            int u = u0, k = k0;
-            for (int idx = tid; idx < line_elems; idx += nthr) {
-                const float *src = f + __float_as_int(seg[u].x) + k;
-                if (k < npair) cp_async4(&dst[k * LINE_PITCH + u].x, src);   // first of pair k
-                if (k >= 1) cp_async4(&dst[(k - 1) * LINE_PITCH + u].y, src); // second of pair k - 1
-                k += dk;
+            float *dst = sLine + buf * SG * pitch;
+            const int *col = sCol + chunk * SG;
+            for (int u = u_0, i = i_0; u < SG;) {
+                const int c0 = col[u];
+                const int first = c0 & ~3, last = (c0 + G.nz + 3) & ~3; // 16-byte rounded line
+                if (first + 4 * i < last) cp_async16(dst + u * pitch + 4 * i, f + first + 4 * i);
                 u += du;
-                if (k >= G.nz) {
-                    k -= G.nz;
+                i += di;
+                if (i >= quads) {
+                    i -= quads;
                     ++u;
                 }
             }
@@ -278,7 +298,7 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
         fill(0, 0);
         float g0 = tau_in;
         for (int ch = 0; ch < nchunk; ++ch) {
-            const int j = ch * SEG_GROUP;
+            const int j = ch * SG;
             if (ch + 1 < nchunk) {
                 fill(ch + 1, (ch + 1) & 1);
                 cp_async_wait<1>();
@@ -286,8 +306,8 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
                 cp_async_wait<0>();
             }
             __syncthreads();
-            const float2 *pairs = sPair + (ch & 1) * npair * LINE_PITCH;
-            const float gend = sEnd[j + SEG_GROUP - 1];
+            const float *lines = sLine + (ch & 1) * SG * pitch;
+            const float gend = sEnd[j + SG - 1];
             int knew[R];
             bool anew[R];
             float tz2[R];
@@ -301,40 +321,44 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
                              ? tau_zplane(plane_at(knew[r] + (skz[r] > 0), G.dz, G.z0), inv_v[r], G.tc) : P_INF;
                 dense = dense || tz2[r] < gend;
             }
-            if (G.nz >= 2 && !__any_sync(0xffffffffu, dense)) {
-                // voxel pair (kb, kb + 1) holding a row's current slab kz and next slab knew
-                const float2 *base[R];
-                float m_lo[R], m_hi[R], sg[R], hg[R], dt[R], acc_lo[R], acc_hi[R];
+            if (!__any_sync(0xffffffffu, dense)) {
+                // At most one z crossing per row in this group: the row reads its current
+                // slab before the crossing column c and its next slab from c on, then
+                // corrects column c for the part before the crossing. A slab outside the
+                // volume reads the zero line.
+                // 32-bit offsets into shared memory of the current and next slab's voxel in
+                // the group's first line
+                const int lines_off = (int)(lines - smem), zero_off = (int)(sZero - smem);
+                int oc[R], on[R], c[R];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    int kb = anew[r] ? min(kz[r], knew[r]) : (active[r] ? (skz[r] > 0 ? kz[r] - 1 : kz[r]) : 0);
-                    kb = min(max(kb, 0), G.nz - 2);
-                    const bool lo_old = kb == kz[r];
-                    m_lo[r] = ((lo_old && active[r]) || (kb == knew[r] && anew[r])) ? 1.0f : 0.0f;
-                    m_hi[r] = ((kb + 1 == kz[r] && active[r]) || (kb + 1 == knew[r] && anew[r])) ? 1.0f : 0.0f;
-                    // the lower voxel takes the part before the crossing if it is the current slab
-                    sg[r] = lo_old ? 1.0f : -1.0f;
-                    hg[r] = lo_old ? 0.0f : 1.0f;
-                    dt[r] = fminf(tzn[r], 1e30f) - g0;
-                    base[r] = pairs + kb * LINE_PITCH;
-                    acc_lo[r] = 0.0f;
-                    acc_hi[r] = 0.0f;
+                    oc[r] = active[r] ? lines_off + kz[r] : zero_off;
+                    on[r] = anew[r] ? lines_off + knew[r] : zero_off;
+                    // c = number of segment ends of the group at or before the crossing
+                    int cr = 0;
+#pragma unroll
+                    for (int step = SG / 2; step >= 1; step >>= 1)
+                        if (sEnd[j + cr + step - 1] <= tzn[r]) cr += step;
+                    if (sEnd[j + cr] <= tzn[r]) ++cr;
+                    c[r] = cr;
                 }
 #pragma unroll
-                for (int u = 0; u < SEG_GROUP; ++u) {
-                    const float4 sg4 = sSeg[j + u]; // (column, length, 1/length, start term)
+                for (int u = 0; u < SG; ++u) {
+                    const float2 seg = sSeg[j + u]; // (line offset, length)
+                    const int lo = __float_as_int(seg.x);
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
-                        const float flo = __saturatef(fmaf(sg[r], fmaf(dt[r], sg4.z, sg4.w), hg[r]));
-                        const float wlo = sg4.y * flo, whi = sg4.y - wlo;
-                        const float2 v = base[r][u];
-                        acc_lo[r] = fmaf(v.x, wlo, acc_lo[r]);
-                        acc_hi[r] = fmaf(v.y, whi, acc_hi[r]);
+                        const int o = u < c[r] ? oc[r] : on[r];
+                        acc[r] = fmaf(smem[o + lo], seg.y, acc[r]);
                     }
                 }
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    acc[r] = fmaf(m_lo[r], acc_lo[r], fmaf(m_hi[r], acc_hi[r], acc[r]));
+                    if (c[r] < SG) {
+                        const int lo = __float_as_int(sSeg[j + c[r]].x);
+                        const float start = c[r] ? sEnd[j + c[r] - 1] : g0;
+                        acc[r] = fmaf(smem[oc[r] + lo] - smem[on[r] + lo], fmaxf(tzn[r] - start, 0.0f), acc[r]);
+                    }
                     if (tzn[r] < gend) {
                         kz[r] = knew[r];
                         active[r] = anew[r];
@@ -346,24 +370,19 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
 #pragma unroll 1
-                    for (int u = 0; u < SEG_GROUP; ++u) {
+                    for (int u = 0; u < SG; ++u) {
                         const float e = sEnd[j + u];
                         float sl = u ? sEnd[j + u - 1] : g0;
+                        const float *line = lines + __float_as_int(sSeg[j + u].x);
                         while (tzn[r] < e) {
-                            if (active[r])
-                                acc[r] = fmaf(kz[r] < npair ? pairs[kz[r] * LINE_PITCH + u].x
-                                                            : pairs[(kz[r] - 1) * LINE_PITCH + u].y,
-                                              tzn[r] - sl, acc[r]);
+                            if (active[r]) acc[r] = fmaf(line[kz[r]], tzn[r] - sl, acc[r]);
                             sl = tzn[r];
                             kz[r] += skz[r];
                             active[r] = (unsigned)kz[r] < (unsigned)G.nz;
                             tzn[r] = active[r] ? tau_zplane(plane_at(kz[r] + (skz[r] > 0), G.dz, G.z0), inv_v[r], G.tc)
                                                : P_INF;
                         }
-                        if (active[r])
-                            acc[r] = fmaf(kz[r] < npair ? pairs[kz[r] * LINE_PITCH + u].x
-                                                        : pairs[(kz[r] - 1) * LINE_PITCH + u].y,
-                                          e - sl, acc[r]);
+                        if (active[r]) acc[r] = fmaf(line[kz[r]], e - sl, acc[r]);
                     }
                 }
             }
@@ -410,25 +429,32 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
 }
 
 // per-device record of the shared-memory opt-in, one per kernel instantiation
-template <int MODE, typename TP> static std::atomic<unsigned long long> g_project_optin{0};
+// per-device record of the shared-memory opt-in, one per kernel instantiation
+template <int MODE, typename TP, int SG> static std::atomic<unsigned long long> g_project_optin{0};
 
 template <int MODE, typename TP> static cbct_status project_optin()
 {
-    cudaError_t e = smem_optin_once(k_project<MODE, TP>, 200 * 1024, g_project_optin<MODE, TP>);
+    cudaError_t e = smem_optin_once(k_project<MODE, TP, SEG_GROUP_MAX>, 200 * 1024, g_project_optin<MODE, TP, SEG_GROUP_MAX>);
+    if (e == cudaSuccess)
+        e = smem_optin_once(k_project<MODE, TP, SEG_GROUP_MAX / 2>, 200 * 1024, g_project_optin<MODE, TP, SEG_GROUP_MAX / 2>);
     return e == cudaSuccess ? CBCT_OK : check_cuda(e, "project attribute");
 }
 
 template <int MODE, typename TP>
 static cbct_status launch_project_t(const GeomDev &G, const float *f, int isx, int isy, const float *y, void *out,
                                    double *partials, float count_thr, const Scalars *sc, dim3 grid, int threads,
-                                   size_t smem, cudaStream_t st)
+                                   int sg, size_t smem, cudaStream_t st)
 {
     {
         cbct_status a = project_optin<MODE, TP>();
         if (a != CBCT_OK) return a;
     }
-    k_project<MODE, TP><<<grid, threads, smem, st>>>(G, f, isx, isy, y, static_cast<TP *>(out),
-                                                    partials, count_thr, sc);
+    if (sg == SEG_GROUP_MAX)
+        k_project<MODE, TP, SEG_GROUP_MAX><<<grid, threads, smem, st>>>(G, f, isx, isy, y, static_cast<TP *>(out),
+                                                                       partials, count_thr, sc);
+    else
+        k_project<MODE, TP, SEG_GROUP_MAX / 2><<<grid, threads, smem, st>>>(G, f, isx, isy, y, static_cast<TP *>(out),
+                                                                           partials, count_thr, sc);
     return CBCT_OK;
 }
 
@@ -454,7 +480,8 @@ cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long 
 {
     const int threads = proj_threads(G); // 2 rows each
     dim3 grid((unsigned)(G.nviews * G.nu), (unsigned)((G.nv + 2 * threads - 1) / (2 * threads)));
-    const size_t smem = project_smem(G);
+    const int sg = segment_group(G);
+    const size_t smem = project_smem(G, sg);
     if (smem > 200 * 1024)
         return set_error(CBCT_ERR_UNSUPPORTED, "project: grid too large for the projector's shared memory (nx + ny and nz)");
     if (sz != 1) return set_error(CBCT_ERR_INVALID_ARG, "project: the volume must be z-contiguous");
@@ -463,27 +490,27 @@ cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long 
     ProfToken tok = prof_start(CBCT_KERNEL_PROJECT, st);
     if (mode == PM_PLAIN) {
         if (storage == ST_BF16)
-            r = launch_project_t<PM_PLAIN, __nv_bfloat16>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+            r = launch_project_t<PM_PLAIN, __nv_bfloat16>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
         else if (storage == ST_F16)
-            r = launch_project_t<PM_PLAIN, __half>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+            r = launch_project_t<PM_PLAIN, __half>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
         else
-            r = launch_project_t<PM_PLAIN, float>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+            r = launch_project_t<PM_PLAIN, float>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
     } else if (mode == PM_COUNT) {
-        r = launch_project_t<PM_COUNT, float>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+        r = launch_project_t<PM_COUNT, float>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
     } else if (mode == PM_Q_SCALED) {
         if (storage == ST_BF16)
-            r = launch_project_t<PM_Q_SCALED, __nv_bfloat16>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+            r = launch_project_t<PM_Q_SCALED, __nv_bfloat16>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
         else if (storage == ST_F16)
-            r = launch_project_t<PM_Q_SCALED, __half>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+            r = launch_project_t<PM_Q_SCALED, __half>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
         else
-            r = launch_project_t<PM_Q_SCALED, float>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+            r = launch_project_t<PM_Q_SCALED, float>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
     } else {
         if (storage == ST_BF16)
-            r = launch_project_t<PM_RESID, __nv_bfloat16>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+            r = launch_project_t<PM_RESID, __nv_bfloat16>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
         else if (storage == ST_F16)
-            r = launch_project_t<PM_RESID, __half>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+            r = launch_project_t<PM_RESID, __half>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
         else
-            r = launch_project_t<PM_RESID, float>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, smem, st);
+            r = launch_project_t<PM_RESID, float>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
     }
     prof_stop(tok, st);
     note_launch();

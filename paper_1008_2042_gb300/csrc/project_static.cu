@@ -12,9 +12,10 @@
 
 namespace cbct {
 
-// Fixed scratch: the z-contiguous copy of the input volume. Every GPU that loads the
-// library holds this array (16 MiB) until the process exits.
-static __device__ __align__(256) float g_static_volume[CBCT_PROJECT_STATIC_MAX_VOXELS];
+// Fixed scratch: the z-contiguous copy of the input volume, plus the slack the projector
+// may read past a volume's end. Every GPU that loads the library holds this array (16 MiB)
+// until the process exits.
+static __device__ __align__(256) float g_static_volume[CBCT_PROJECT_STATIC_MAX_VOXELS + PROJECT_VOLUME_SLACK / 4];
 
 // In host code `g_static_volume` names a host-side stand-in, not device memory, so the
 // device address is looked up once per device (with that device current) and cached.

@@ -360,8 +360,9 @@ static size_t work_layout(const cbct_geometry *g, char *base, Work *w)
         off += align256(bytes);
         return p;
     };
-    float *X = (float *)take(4 * N), *X2 = (float *)take(4 * N), *P = (float *)take(4 * N), *S = (float *)take(4 * N);
-    float *Fa = (float *)take(4 * N), *Fb = (float *)take(4 * N);
+    const size_t VB = 4 * N + PROJECT_VOLUME_SLACK; // volumes the projector may read past the end
+    float *X = (float *)take(VB), *X2 = (float *)take(VB), *P = (float *)take(VB), *S = (float *)take(VB);
+    float *Fa = (float *)take(VB), *Fb = (float *)take(VB);
     void *R = take(4 * M), *Q = take(4 * M); // sized for FP32, the widest storage type
     float2 *PS = (float2 *)take(sizeof(float2) * prefix_elems(d));
     double *partials = (double *)take(sizeof(double) * max_partials(g));
@@ -559,7 +560,7 @@ extern "C" cbct_status cbct_project_ex(const cbct_geometry *gc, const float *f, 
     cbct_geometry *g = const_cast<cbct_geometry *>(gc);
     const GeomDev G = level_geom(g, 0);
     const size_t N = (size_t)G.nx * G.ny * G.nz;
-    TRY(ensure_scratch(g, sizeof(float) * N));
+    TRY(ensure_scratch(g, sizeof(float) * N + PROJECT_VOLUME_SLACK));
     cudaStream_t st = (cudaStream_t)stream;
     float *fz = g->d_scratch;
     TRY(transpose(f, fz, G.nx, G.ny, G.nz, true, st));

@@ -5,6 +5,7 @@ Nsight Compute captures and quick timings of a single kernel.
 
 --op: project | backproject | tf_analyze | tf_synth | reconstruct
 --shape: paper (512x512x70, 512x384 imager, 40 views) | small (64x64x16, 128x32, 40 views)
+         | iso256 (256x256x64 at 1 mm, 256x192 imager at 1.5 mm, 60 views)
 --level: multigrid level of the operator's grid (0 = finest; project/backproject only)
 Prints the mean device time per call (CUDA events) after one untimed call.
 """
@@ -31,14 +32,20 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--op", default="project",
                     choices=("project", "backproject", "tf_analyze", "tf_synth", "reconstruct"))
-    ap.add_argument("--shape", default="paper", choices=("paper", "small"))
+    ap.add_argument("--shape", default="paper", choices=("paper", "small", "iso256"))
     ap.add_argument("--views", type=int, default=40)
     ap.add_argument("--level", type=int, default=0)
     ap.add_argument("--repeat", type=int, default=3)
     a = ap.parse_args(argv)
 
     cuda_build.build()
-    geom = synth.config_paper(a.views) if a.shape == "paper" else synth.config_small(a.views)
+    if a.shape == "paper":
+        geom = synth.config_paper(a.views)
+    elif a.shape == "iso256":
+        geom = synth.Geometry(nx=256, ny=256, nz=64, dx=1.0, dy=1.0, dz=1.0, nu=256, nv=192, du=1.5, dv=1.5,
+                              n_views=a.views if a.views != 40 else 60)
+    else:
+        geom = synth.config_small(a.views)
     geom = geom.level(a.level) if a.level else geom
     dev = torch.device("cuda")
     g = cb.Geometry(geom)
