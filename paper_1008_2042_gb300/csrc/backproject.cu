@@ -21,12 +21,15 @@
 namespace cbct {
 
 constexpr int BP_TX = 32, BP_TY = 4;
+#ifndef CBCT_BP_MAX_ZC
+#define CBCT_BP_MAX_ZC 8 // z voxels per thread at most (8 or 16)
+#endif
 
 static int bp_zchunk(const GeomDev &G)
 {
     const long long tiles = (long long)((G.nx + BP_TX - 1) / BP_TX) * ((G.ny + BP_TY - 1) / BP_TY);
     const long long want = 4LL * device_sm_count();
-    int zc = 8;
+    int zc = CBCT_BP_MAX_ZC;
     while (zc > 1 && tiles * ((G.nz + zc - 1) / zc) < want) zc >>= 1;
     return zc;
 }
@@ -52,8 +55,9 @@ __device__ __forceinline__ void straddle_rows(const GeomDev &G, float zp, float 
 
 // Rows reaching plane zp inside the column lie in the window [a, b) of imager rows (at
 // most one row when the caller's `simple` test holds); a and b are clamped to [0, nv] so
-// that col[a], col[b] are valid prefixes. Returns those prefixes and the straddling row's
-// weighted contributions below and above the plane (zero if the window is empty).
+// that the prefixes col[a * nu], col[b * nu] exist (the table is [view][row][column]).
+// Returns those prefixes and the straddling row's weighted contributions below and above
+// the plane (zero if the window is empty).
 __device__ __forceinline__ void plane_terms(const GeomDev &G, const float *s_invv, const float2 *col, float zp,
                                             float A, float B, float ta, float tb, float c0, float c1,
                                             float2 &Pa, float2 &Pb, float &below, float &above)
@@ -63,8 +67,29 @@ __device__ __forceinline__ void plane_terms(const GeomDev &G, const float *s_inv
     const float fa = fminf(fmaxf(fmaf(fminf(v0, v1), G.inv_dv, c0), 0.0f), nvf);
     const float fb = fminf(fmaxf(fmaf(fmaxf(v0, v1), G.inv_dv, c1), -1.0f), nvf - 1.0f);
     const int a = ceil_small(fa), b = floor_small(fb) + 1;
-    Pa = __ldg(col + a);
-    Pb = __ldg(col + max(a, b));
+    Pa = __ldg(col + a * G.nu); // (nv + 1) * nu < 2^31: 32-bit offsets
+    Pb = __ldg(col + max(a, b) * G.nu);
+    const float g = (Pb.x - Pa.x) + (Pb.y - Pa.y);
+    const float iw = s_invv[min(a, G.nv - 1)];
+    const float scl = fminf(fmaxf(tau_zplane(zp, iw, G.tc), ta), tb);
+    const float wlo = scl - ta, whi = tb - scl;
+    const bool up = iw > 0.0f; // z grows along the ray (v >= 0)
+    below = g * (up ? wlo : whi);
+    above = g * (up ? whi : wlo);
+}
+
+// plane_terms for a window known to lie on the imager (0 <= fa, fb <= nv - 1 for every
+// plane of the chunk, checked by the caller at the extreme planes: both bounds grow with
+// the plane height). zs = zp / dv; (lo_f, hi_f) = (B, A) above z = 0 and (A, B) below, so
+// the window's lower and upper row bounds are zs * lo_f and zs * hi_f.
+__device__ __forceinline__ void plane_terms_inside(const GeomDev &G, const float *s_invv, const float2 *col,
+                                                   float zp, float zs, float lo_f, float hi_f, float ta, float tb,
+                                                   float c0, float c1, float2 &Pa, float2 &Pb, float &below,
+                                                   float &above)
+{
+    const int a = ceil_small(fmaf(zs, lo_f, c0)), b = floor_small(fmaf(zs, hi_f, c1)) + 1;
+    Pa = __ldg(col + a * G.nu);
+    Pb = __ldg(col + max(a, b) * G.nu);
     const float g = (Pb.x - Pa.x) + (Pb.y - Pa.y);
     const float iw = s_invv[min(a, G.nv - 1)];
     const float scl = fminf(fmaxf(tau_zplane(zp, iw, G.tc), ta), tb);
@@ -99,12 +124,15 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
     if (ok) {
         const float xl = plane_at(ix, G.dx, G.x0), xh = plane_at(ix + 1, G.dx, G.x0);
         const float yl = plane_at(iy, G.dy, G.y0), yh = plane_at(iy + 1, G.dy, G.y0);
-        float zp[ZC + 1];
+        float zp[ZC + 1], zs[ZC + 1];
 #pragma unroll
-        for (int z = 0; z <= ZC; ++z) zp[z] = plane_at(iz0 + z, G.dz, G.z0);
+        for (int z = 0; z <= ZC; ++z) {
+            zp[z] = plane_at(iz0 + z, G.dz, G.z0);
+            zs[z] = zp[z] * G.inv_dv;
+        }
         const int nzc = min(ZC, G.nz - iz0); // valid voxels in this chunk
         const float zabs = fmaxf(fabsf(zp[0]), fabsf(plane_at(iz0 + nzc, G.dz, G.z0)));
-        const size_t col_stride = (size_t)G.nv + 1;
+        const size_t view_stride = ((size_t)G.nv + 1) * G.nu;
         const float c0 = fmaf(-G.v_first, G.inv_dv, -1e-3f), c1 = fmaf(-G.v_first, G.inv_dv, 1e-3f);
 
         for (int k = 0; k < G.nviews; ++k) {
@@ -133,13 +161,35 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
                 if (!(tb > ta)) continue;
                 const float A = __fdividef(1.0f, G.tc + ta), B = __fdividef(1.0f, G.tc + tb);
                 const float wfull = tb - ta;
-                const float2 *col = ps + ((size_t)k * G.nu + iu) * col_stride;
+                const float2 *col = ps + (size_t)k * view_stride + iu; // prefix m at col[m * nu]
                 // Plane z = zp is reached by the rows with v between zp*A and zp*B. While that
                 // window is shorter than a row pitch and adjacent planes' windows are apart,
                 // every row crosses at most one plane inside the column (the usual case).
                 const float span = zabs * (A - B) * G.inv_dv;
                 const bool simple = span + 3e-3f < 1.0f && fmaf(G.dz * B, G.inv_dv, -span) > 3e-3f;
-                if (simple) {
+                // row-window bounds at the lowest and highest plane of the chunk (monotone
+                // in the plane height, so these bound every plane's window)
+                const float fa_lo = fmaf(zs[0], zs[0] >= 0.0f ? B : A, c0);
+                const float fb_hi = fmaf(zs[nzc], zs[nzc] >= 0.0f ? A : B, c1);
+                if (simple && fa_lo >= 0.0f && fb_hi <= (float)(G.nv - 1)) {
+                    // every window lies on the imager: no clamping
+                    float2 Pa, Pb;
+                    float below, above;
+                    plane_terms_inside(G, s_invv, col, zp[0], zs[0], zs[0] >= 0.0f ? B : A, zs[0] >= 0.0f ? A : B,
+                                       ta, tb, c0, c1, Pa, Pb, below, above);
+                    acc[0] += above;
+                    float2 Pprev = Pb;
+#pragma unroll
+                    for (int z = 0; z < ZC; ++z) {
+                        if (z >= nzc) break;
+                        const bool pos = zs[z + 1] >= 0.0f;
+                        plane_terms_inside(G, s_invv, col, zp[z + 1], zs[z + 1], pos ? B : A, pos ? A : B, ta, tb,
+                                           c0, c1, Pa, Pb, below, above);
+                        acc[z] = fmaf(wfull, (Pa.x - Pprev.x) + (Pa.y - Pprev.y), acc[z]) + below;
+                        if (z + 1 < ZC && z + 1 < nzc) acc[z + 1] += above;
+                        Pprev = Pb;
+                    }
+                } else if (simple) {
                     // rows strictly between two planes' windows stay in the slab across the
                     // column (weight tb - ta) and are summed as a prefix difference; the one
                     // row in a plane's window is split at the plane
@@ -167,7 +217,7 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
                         float a = acc[z];
                         const int f0 = max(hi_p + 1, 0), f1 = min(lo_n - 1, G.nv - 1);
                         if (f0 <= f1) {
-                            const float2 P1 = __ldg(col + f1 + 1), P0 = __ldg(col + f0);
+                            const float2 P1 = __ldg(col + (f1 + 1) * G.nu), P0 = __ldg(col + f0 * G.nu);
                             a = fmaf(wfull, (P1.x - P0.x) + (P1.y - P0.y), a);
                         }
                         // rows that cross a z plane inside the column: exact overlap
@@ -181,7 +231,7 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
                             const float s0 = tau_zplane(zp[z], iw, G.tc), s1 = tau_zplane(zp[z + 1], iw, G.tc);
                             const float lo = fmaxf(ta, fminf(s0, s1)), hi = fminf(tb, fmaxf(s0, s1));
                             if (hi > lo) {
-                                const float2 Q1 = __ldg(col + iv + 1), Q0 = __ldg(col + iv);
+                                const float2 Q1 = __ldg(col + (iv + 1) * G.nu), Q0 = __ldg(col + iv * G.nu);
                                 a = fmaf((Q1.x - Q0.x) + (Q1.y - Q0.y), hi - lo, a);
                             }
                         }
@@ -230,6 +280,9 @@ cbct_status launch_backproject(const GeomDev &G, const float2 *ps, float *out, l
     const int isx = (int)sx, isy = (int)sy, isz = (int)sz;
     ProfToken tok = prof_start(CBCT_KERNEL_BACKPROJECT, st);
     switch (zc) {
+#if CBCT_BP_MAX_ZC >= 16
+    case 16: k_backproject<16><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials); break;
+#endif
     case 8: k_backproject<8><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials); break;
     case 4: k_backproject<4><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials); break;
     case 2: k_backproject<2><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials); break;
@@ -240,8 +293,9 @@ cbct_status launch_backproject(const GeomDev &G, const float2 *ps, float *out, l
     return check_cuda(cudaGetLastError(), "backproject launch");
 }
 
-// Prefix sums over imager rows of every (view k, imager column iu):
-// ps[k][iu][m] = sum_{iv < m} w(iv) g[k][iv][iu], m = 0..nv, with w = |D - S| if
+// Prefix sums over imager rows of every (view k, imager column iu), stored row-major like
+// the projections so that neighbouring lanes (columns) touch neighbouring addresses:
+// ps[k][m][iu] = sum_{iv < m} w(iv) g[k][iv][iu], m = 0..nv, with w = |D - S| if
 // `prescale` (folds the ray length into the adjoint's input) and 1 otherwise. Sums are
 // accumulated in FP64 and stored as a float pair (hi, lo = remainder), so differences of
 // two prefixes keep FP32 relative accuracy however long the column. A block covers 32
@@ -278,14 +332,14 @@ k_row_prefix(GeomDev G, const T *__restrict__ g, float2 *__restrict__ ps, int pr
     double run = 0.0;
     for (int c = 0; c < w; ++c) run += s_tot[c][lane];
     if (!ok) return;
-    float2 *dst = ps + ((size_t)k * G.nu + iu) * ((size_t)G.nv + 1);
+    float2 *dst = ps + (size_t)k * ((size_t)G.nv + 1) * G.nu + iu; // prefix m at dst[m * nu]
     if (w == 0) dst[0] = make_float2(0.0f, 0.0f);
     for (int iv = r0; iv < r1; ++iv) {
         float val = load_as_float(src + (size_t)iv * G.nu);
         if (prescale) val *= ray_length(dxr, dyr, imager_v(G, iv));
         run += (double)val;
         const float hi = (float)run;
-        dst[iv + 1] = make_float2(hi, (float)(run - (double)hi));
+        dst[(size_t)(iv + 1) * G.nu] = make_float2(hi, (float)(run - (double)hi));
     }
 }
 
