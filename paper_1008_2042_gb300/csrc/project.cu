@@ -5,12 +5,14 @@
 // transverse path through the (x, y) voxel columns; the imager row v only tilts them in
 // z. A block owns one (view, column) pair and its threads own the imager rows. The
 // block first computes the shared transverse Siddon trace once, cooperatively, into
-// shared memory (a parallel merge of the x-plane and y-plane crossing lists). Each lane
-// then walks that list, reading the voxel of its own z slab in every column; with the
-// iteration's z-fastest volume layout the 32 lanes of a warp read a few consecutive
-// floats of one column, one or two 32-byte sectors per load. Columns are processed in
-// unrolled groups whose loads are all in flight together; the rare columns in which a
-// lane crosses a z plane are corrected afterwards. Accumulation is FP32; the epilogue can
+// shared memory (a parallel merge of the x-plane and y-plane crossing lists). Along that
+// trace a ray of row v stays in one z slab for long runs of columns (the cone is narrow),
+// and the block holds more rows than the volume has slabs. So, group by group of
+// columns, the block stages the columns' z-lines (contiguous in the iteration's
+// z-fastest layout) and forms per slab the running sum of voxel value x segment length;
+// a row's line integral over a run of columns in one slab is then the difference of two
+// table entries, and only the columns where it crosses a z plane are split explicitly.
+// Accumulation is FP32; the epilogue can
 // scale by |D - S|, form the CGLS residual and reduce squared norms in FP64 into one
 // partial per block; the output is stored as FP32, BF16 or FP16.
 #include <cfloat>
@@ -40,9 +42,8 @@ int project_num_blocks(const GeomDev &G)
     return G.nviews * G.nu * ((G.nv + rows - 1) / rows);
 }
 
-// Column segments a lane processes per unrolled group: 32 where the geometry guarantees at
-// most one z-plane crossing per row in any 32 consecutive segments, else 16 (rows that
-// cross twice in a group take the exact sequential walk).
+// Column segments per group (one staged set of z-lines and one prefix table): 32, or 16
+// where the shared memory of 32 would not fit.
 constexpr int SEG_GROUP_MAX = 32;
 
 __device__ __forceinline__ int lower_count(const float *a, int n, float t) // # a[i] < t
@@ -72,13 +73,11 @@ static inline int seg_capacity(const GeomDev &G, int sg)
     return ((G.nx + G.ny + 3 + sg - 1) / sg + 1) * sg;
 }
 
-// The z distance a row covers over sg segments is at most (its z slope) x sg x (the voxel
-// column diagonal); the slope is |v| / (transverse source-pixel distance) <= max|v| / sdd.
+static inline size_t project_smem(const GeomDev &G, int sg);
+
 static inline int segment_group(const GeomDev &G)
 {
-    const double vmax = fmax(fabs((double)G.v_first), fabs((double)G.v_first + (G.nv - 1) * (double)G.dv));
-    const double diag = sqrt((double)G.dx * G.dx + (double)G.dy * G.dy);
-    return vmax / G.sdd * SEG_GROUP_MAX * diag < 0.95 * G.dz ? SEG_GROUP_MAX : SEG_GROUP_MAX / 2;
+    return project_smem(G, SEG_GROUP_MAX) <= 200 * 1024 ? SEG_GROUP_MAX : SEG_GROUP_MAX / 2;
 }
 
 // Shared memory of one block: the two crossing lists, then (16-byte aligned) per segment
@@ -94,12 +93,11 @@ static inline int seg_offset(const GeomDev &G) { return ((G.nx + G.ny + 2 + 3) /
 static inline int line_pitch(int nz) { return ((nz + 6 + 3) / 4) * 4; }
 
 // shared memory: crossing lists, per segment (end tau, column offset, (line offset,
-// length)), two staged groups of z-lines and one group-sized line of zeros (read by rows
-// outside the volume)
+// length)), two staged groups of z-lines and the group's per-slab prefix table
 static inline size_t project_smem(const GeomDev &G, int sg)
 {
     return sizeof(float) * (size_t)seg_offset(G) + (sizeof(float) + sizeof(int) + sizeof(float2)) * (size_t)seg_capacity(G, sg) +
-           sizeof(float) * 3 * (size_t)sg * line_pitch(G.nz);
+           sizeof(float) * (2 * (size_t)sg * line_pitch(G.nz) + (size_t)G.nz * (sg + 1));
 }
 
 size_t project_smem_bytes(const GeomDev &G) { return project_smem(G, segment_group(G)); }
@@ -119,12 +117,11 @@ template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile(
 // crossing's position in the merged order is its own index plus the number of crossings
 // of the other family before it (binary search); this yields the list of (x, y) voxel
 // columns the rays visit and the tau at which each is left. For every segment the block
-// also stores its length, 1 / length and its start relative to its group.
-// Phase 2 (one lane per imager row): walk the list in groups of SG columns. In a
-// group a lane crosses at most one z plane (else an exact sequential walk is used): it
-// reads the voxel pair (kb, kb + 1) around its current and next slab in every column and
-// splits each column's length at its crossing with a saturated FMA. No branch and no
-// integer or compare instruction is spent per column.
+// also stores its length and where its column's z-line will sit in shared memory.
+// Phase 2, per group of SG segments: the block stages the group's z-lines and builds
+// the per-slab prefix table T[k][u] over the group's columns; then each thread (two
+// imager rows) adds, for each run of whole columns a row spends in one z slab, the
+// table difference, and splits exactly each column in which the row crosses a z plane.
 template <int MODE, typename TP, int SG>
 __global__ void __launch_bounds__(PROJ_THREADS, CBCT_PROJ_MIN_BLOCKS)
 k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *__restrict__ y,
@@ -141,7 +138,8 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
     const int pitch = ((G.nz + 6 + 3) / 4) * 4;            // floats per staged line
     const int quads = pitch / 4;                           // 16-byte pieces per line slot
     float *sLine = reinterpret_cast<float *>(sSeg + cap);  // two staged groups of z-lines
-    float *sZero = sLine + 2 * SG * pitch;                 // zeros, as long as one group
+    constexpr int TPITCH = SG + 1;
+    float *sTab = sLine + 2 * SG * pitch;                  // [nz][SG + 1] per-slab prefix table
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int view = blockIdx.x / G.nu;
@@ -224,7 +222,6 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
         const int loff = (q % SG) * pitch + (sCol[q] & 3);
         sSeg[q] = make_float2(__int_as_float(loff), sEnd[q] - st);
     }
-    for (int q = tid; q < SG * pitch; q += nthr) sZero[q] = 0.0f;
     __syncthreads();
 
     // ---- phase 2: per-row z state (two rows per thread: iv[0] and iv[1] = iv[0] + nthr) ----
@@ -272,8 +269,14 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
             }
         }
     } else if (hit) {
-        // Stage the z-lines of each group of columns into shared memory one group ahead
-        // (16-byte cp.async), then let every row read its voxel pair there.
+        // Per group of SG segments: stage the z-lines of its columns (16-byte cp.async,
+        // one group ahead), build once for the block the per-slab prefix table over the
+        // group's columns,
+        //     T[k][u] = sum_{u' < u} f(column u', slab k) * length(u'),   u = 0..SG,
+        // and let every row add T[k][u1] - T[k][u0] for each run of whole columns it
+        // spends in slab k. Only the columns in which a row crosses a z plane are split,
+        // exactly, at the crossing. A block has far more rows than slabs, so the table
+        // does the per-column work once per slab instead of once per row.
         const int nchunk = (nseg + SG - 1) / SG;
         // 16-byte pieces of a group's lines: slot c = (line u, piece i), c = u * quads + i;
         // thread tid takes c = tid, tid + nthr, ... (the same slots for every group)
@@ -295,6 +298,12 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
             }
             cp_async_commit();
         };
+        const bool split = nthr >= 2 * G.nz;
+        // T[k][u]: the table entry, plus the first half's total for a second-half entry
+        auto tab = [&](int k, int u) {
+            const float *trow = sTab + k * TPITCH;
+            return split && u > SG / 2 ? trow[u] + trow[SG / 2] : trow[u];
+        };
         fill(0, 0);
         float g0 = tau_in;
         for (int ch = 0; ch < nchunk; ++ch) {
@@ -307,84 +316,73 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
             }
             __syncthreads();
             const float *lines = sLine + (ch & 1) * SG * pitch;
-            const float gend = sEnd[j + SG - 1];
-            int knew[R];
-            bool anew[R];
-            float tz2[R];
-            bool dense = false;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                knew[r] = kz[r] + skz[r];
-                anew[r] = active[r] && (unsigned)knew[r] < (unsigned)G.nz;
-                // the crossing after tzn, to detect two crossings inside one group
-                tz2[r] = (tzn[r] < gend && anew[r])
-                             ? tau_zplane(plane_at(knew[r] + (skz[r] > 0), G.dz, G.z0), inv_v[r], G.tc) : P_INF;
-                dense = dense || tz2[r] < gend;
-            }
-            if (!__any_sync(0xffffffffu, dense)) {
-                // At most one z crossing per row in this group: the row reads its current
-                // slab before the crossing column c and its next slab from c on, then
-                // corrects column c for the part before the crossing. A slab outside the
-                // volume reads the zero line.
-                // 32-bit offsets into shared memory of the current and next slab's voxel in
-                // the group's first line
-                const int lines_off = (int)(lines - smem), zero_off = (int)(sZero - smem);
-                int oc[R], on[R], c[R];
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    oc[r] = active[r] ? lines_off + kz[r] : zero_off;
-                    on[r] = anew[r] ? lines_off + knew[r] : zero_off;
-                    // c = number of segment ends of the group at or before the crossing
-                    int cr = 0;
-#pragma unroll
-                    for (int step = SG / 2; step >= 1; step >>= 1)
-                        if (sEnd[j + cr + step - 1] <= tzn[r]) cr += step;
-                    if (sEnd[j + cr] <= tzn[r]) ++cr;
-                    c[r] = cr;
-                }
-#pragma unroll
-                for (int u = 0; u < SG; ++u) {
-                    const float2 seg = sSeg[j + u]; // (line offset, length)
-                    const int lo = __float_as_int(seg.x);
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const int o = u < c[r] ? oc[r] : on[r];
-                        acc[r] = fmaf(smem[o + lo], seg.y, acc[r]);
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (c[r] < SG) {
-                        const int lo = __float_as_int(sSeg[j + c[r]].x);
-                        const float start = c[r] ? sEnd[j + c[r] - 1] : g0;
-                        acc[r] = fmaf(smem[oc[r] + lo] - smem[on[r] + lo], fmaxf(tzn[r] - start, 0.0f), acc[r]);
-                    }
-                    if (tzn[r] < gend) {
-                        kz[r] = knew[r];
-                        active[r] = anew[r];
-                        tzn[r] = tz2[r];
+            // The group's prefix table. With threads to spare each slab's running sum is
+            // split into two chains of SG / 2 columns computed side by side; the second
+            // half's entries then hold sums from column SG / 2 on, and tab() adds the
+            // first half's total.
+            if (split) {
+                for (int task = tid; task < 2 * G.nz; task += nthr) {
+                    const int k = task >> 1, h = (task & 1) * (SG / 2);
+                    float *trow = sTab + k * TPITCH + h;
+                    float sum = 0.0f;
+                    if (!h) trow[0] = 0.0f;
+#pragma unroll 8
+                    for (int u = 0; u < SG / 2; ++u) {
+                        const float2 seg = sSeg[j + h + u]; // (line offset, length)
+                        sum = fmaf(lines[__float_as_int(seg.x) + k], seg.y, sum);
+                        trow[u + 1] = sum;
                     }
                 }
             } else {
-                // a row crosses several z planes in this group (or nz = 1): walk it exactly
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-#pragma unroll 1
+                for (int k = tid; k < G.nz; k += nthr) {
+                    float *trow = sTab + k * TPITCH;
+                    float sum = 0.0f;
+                    trow[0] = 0.0f;
+#pragma unroll 8
                     for (int u = 0; u < SG; ++u) {
-                        const float e = sEnd[j + u];
-                        float sl = u ? sEnd[j + u - 1] : g0;
-                        const float *line = lines + __float_as_int(sSeg[j + u].x);
-                        while (tzn[r] < e) {
-                            if (active[r]) acc[r] = fmaf(line[kz[r]], tzn[r] - sl, acc[r]);
-                            sl = tzn[r];
-                            kz[r] += skz[r];
-                            active[r] = (unsigned)kz[r] < (unsigned)G.nz;
-                            tzn[r] = active[r] ? tau_zplane(plane_at(kz[r] + (skz[r] > 0), G.dz, G.z0), inv_v[r], G.tc)
-                                               : P_INF;
-                        }
-                        if (active[r]) acc[r] = fmaf(line[kz[r]], e - sl, acc[r]);
+                        const float2 seg = sSeg[j + u];
+                        sum = fmaf(lines[__float_as_int(seg.x) + k], seg.y, sum);
+                        trow[u + 1] = sum;
                     }
                 }
+            }
+            __syncthreads();
+            const float gend = sEnd[j + SG - 1];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float a = acc[r];
+                int first = 0;      // first column of the group not yet accounted
+                int cpend = -1;     // column whose remainder from tlast on is the current slab's
+                float tlast = 0.0f;
+                while (tzn[r] < gend) { // a z crossing inside this group (the row is active)
+                    const float t = tzn[r];
+                    int c = 0; // the column holding the crossing: number of group ends <= t
+#pragma unroll
+                    for (int step = SG / 2; step >= 1; step >>= 1)
+                        if (sEnd[j + c + step - 1] <= t) c += step;
+                    if (sEnd[j + c] <= t) ++c;
+                    const float fcur = lines[__float_as_int(sSeg[j + c].x) + kz[r]];
+                    if (c == cpend) {
+                        a = fmaf(fcur, t - tlast, a);
+                    } else {
+                        if (cpend >= 0)
+                            a = fmaf(lines[__float_as_int(sSeg[j + cpend].x) + kz[r]], sEnd[j + cpend] - tlast, a);
+                        a += tab(kz[r], c) - tab(kz[r], first);
+                        a = fmaf(fcur, fmaxf(t - (c ? sEnd[j + c - 1] : g0), 0.0f), a);
+                    }
+                    cpend = c;
+                    tlast = t;
+                    first = c + 1;
+                    kz[r] += skz[r];
+                    active[r] = (unsigned)kz[r] < (unsigned)G.nz;
+                    tzn[r] = active[r] ? tau_zplane(plane_at(kz[r] + (skz[r] > 0), G.dz, G.z0), inv_v[r], G.tc) : P_INF;
+                }
+                if (active[r]) {
+                    if (cpend >= 0)
+                        a = fmaf(lines[__float_as_int(sSeg[j + cpend].x) + kz[r]], sEnd[j + cpend] - tlast, a);
+                    a += tab(kz[r], SG) - tab(kz[r], first);
+                }
+                acc[r] = a;
             }
             g0 = gend;
             __syncthreads();
