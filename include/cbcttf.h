@@ -394,6 +394,9 @@ typedef enum {
  * adds two event records per launch.
  */
 cbct_status cbct_profiling_enable(int enable);
+/* As cbct_profiling_enable, timing only the kinds whose bit (1 << kind) is set in `kinds`
+ * (0 stops timing); untimed launches pay nothing. Events are pooled and reused. */
+cbct_status cbct_profiling_select(unsigned int kinds);
 cbct_status cbct_profiling_reset(void);
 cbct_status cbct_kernel_time(int kind, double *total_ms, unsigned long long *launches);
 

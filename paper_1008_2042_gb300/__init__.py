@@ -101,6 +101,7 @@ _SIGNATURES = {
     "cbct_server_stats_get": [_vp, _vp],
     "cbct_server_destroy": [_vp],
     "cbct_profiling_enable": [_i],
+    "cbct_profiling_select": [ctypes.c_uint],
     "cbct_profiling_reset": [],
     "cbct_kernel_time": [_i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_ulonglong)],
 }
@@ -415,6 +416,14 @@ def count_nnz(geom: Geometry, level: int = 0, stream=None) -> int:
 def profiling(enable: bool) -> None:
     """Bracket every library kernel launch with CUDA events (measurement support)."""
     _check(load_library().cbct_profiling_enable(int(bool(enable))))
+
+
+def profiling_select(kinds) -> None:
+    """Time only the named kernel families (names of KERNEL_KINDS); an empty list stops."""
+    mask = 0
+    for k in kinds:
+        mask |= 1 << KERNEL_KINDS[k]
+    _check(load_library().cbct_profiling_select(mask))
 
 
 def profiling_reset() -> None:

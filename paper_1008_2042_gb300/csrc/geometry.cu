@@ -42,36 +42,49 @@ struct PendingTiming {
     cudaEvent_t a, b;
 };
 static std::mutex g_prof_mu;
-static std::atomic<bool> g_prof_on{false};
+static std::atomic<unsigned> g_prof_mask{0}; // bit k: time launches of kernel kind k
 static std::vector<PendingTiming> g_prof_pending;
+static std::vector<cudaEvent_t> g_prof_pool; // events reused across launches
 static double g_prof_ms[CBCT_KERNEL_KINDS];
 static unsigned long long g_prof_n[CBCT_KERNEL_KINDS];
+
+static cudaEvent_t prof_event()
+{
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        if (!g_prof_pool.empty()) {
+            cudaEvent_t e = g_prof_pool.back();
+            g_prof_pool.pop_back();
+            return e;
+        }
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
 
 ProfToken prof_start(int kind, cudaStream_t st)
 {
     ProfToken t{nullptr, kind};
-    if (!g_prof_on.load(std::memory_order_relaxed)) return t;
+    if (!(g_prof_mask.load(std::memory_order_relaxed) & (1u << kind))) return t;
     // work captured into a CUDA graph is not timed launch by launch
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return t;
-    if (cudaEventCreate(&t.start) != cudaSuccess) {
-        t.start = nullptr;
-        return t;
-    }
-    cudaEventRecord(t.start, st);
+    t.start = prof_event();
+    if (t.start) cudaEventRecord(t.start, st);
     return t;
 }
 
 void prof_stop(const ProfToken &t, cudaStream_t st)
 {
     if (!t.start) return;
-    cudaEvent_t b;
-    if (cudaEventCreate(&b) != cudaSuccess) {
-        cudaEventDestroy(t.start);
+    cudaEvent_t b = prof_event();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!b) {
+        g_prof_pool.push_back(t.start);
         return;
     }
     cudaEventRecord(b, st);
-    std::lock_guard<std::mutex> lk(g_prof_mu);
     g_prof_pending.push_back(PendingTiming{t.kind, t.start, b});
 }
 
@@ -89,8 +102,8 @@ static cbct_status prof_resolve()
         } else if (err == cudaSuccess) {
             err = e;
         }
-        cudaEventDestroy(p.a);
-        cudaEventDestroy(p.b);
+        g_prof_pool.push_back(p.a);
+        g_prof_pool.push_back(p.b);
     }
     g_prof_pending.clear();
     return check_cuda(err, "kernel timing");
@@ -179,12 +192,18 @@ extern "C" const char *cbct_version(void) { return "cbcttf 0.1 (sm_103a)"; }
 
 extern "C" cbct_status cbct_profiling_enable(int enable)
 {
-    if (!enable) {
+    return cbct_profiling_select(enable ? (1u << CBCT_KERNEL_KINDS) - 1u : 0u);
+}
+
+extern "C" cbct_status cbct_profiling_select(unsigned int kinds)
+{
+    if (kinds >> CBCT_KERNEL_KINDS) return set_error(CBCT_ERR_INVALID_ARG, "profiling_select: unknown kernel kind bit");
+    if (!kinds) {
         cbct_status st = prof_resolve();
-        g_prof_on.store(false);
+        g_prof_mask.store(0u);
         return st;
     }
-    g_prof_on.store(true);
+    g_prof_mask.store(kinds);
     return CBCT_OK;
 }
 

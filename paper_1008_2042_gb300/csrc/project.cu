@@ -299,6 +299,7 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
             cp_async_commit();
         };
         const bool split = nthr >= 2 * G.nz;
+        const float inv_dx = 1.0f / G.dx, inv_dy = 1.0f / G.dy;
         // T[k][u]: the table entry, plus the first half's total for a second-half entry
         auto tab = [&](int k, int u) {
             const float *trow = sTab + k * TPITCH;
@@ -356,11 +357,15 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
                 float tlast = 0.0f;
                 while (tzn[r] < gend) { // a z crossing inside this group (the row is active)
                     const float t = tzn[r];
-                    int c = 0; // the column holding the crossing: number of group ends <= t
-#pragma unroll
-                    for (int step = SG / 2; step >= 1; step >>= 1)
-                        if (sEnd[j + c + step - 1] <= t) c += step;
-                    if (sEnd[j + c] <= t) ++c;
+                    // The segment holding the crossing: the x and y planes the ray has passed
+                    // at t, from its transverse position (no search). At a near tie this may
+                    // name the neighbouring segment, which only moves a rounding-sized piece
+                    // of length between two adjacent columns; it is kept monotone.
+                    int na = (int)floorf((fmaf(t, dxr, qx) - G.x0) * inv_dx) - ix_e;
+                    int nb = (int)floorf((fmaf(t, dyr, qy) - G.y0) * inv_dy) - iy_e;
+                    na = min(max(sxs > 0 ? na : -na, 0), nA);
+                    nb = min(max(sys > 0 ? nb : -nb, 0), nB);
+                    const int c = min(max(na + nb - j, max(cpend, 0)), SG - 1);
                     const float fcur = lines[__float_as_int(sSeg[j + c].x) + kz[r]];
                     if (c == cpend) {
                         a = fmaf(fcur, t - tlast, a);
