@@ -297,17 +297,28 @@ cbct_status launch_backproject(const GeomDev &G, const float2 *ps, float *out, l
 // the projections so that neighbouring lanes (columns) touch neighbouring addresses:
 // ps[k][m][iu] = sum_{iv < m} w(iv) g[k][iv][iu], m = 0..nv, with w = |D - S| if
 // `prescale` (folds the ray length into the adjoint's input) and 1 otherwise. Sums are
-// accumulated in FP64 and stored as a float pair (hi, lo = remainder), so differences of
-// two prefixes keep FP32 relative accuracy however long the column. A block covers 32
+// kept as a compensated float pair (sum, correction), so differences of two prefixes keep
+// FP32 relative accuracy however long the column. A block covers 32
 // columns (lanes, coalesced reads) of one view; its 16 warps take consecutive row chunks:
 // pass 1 sums each chunk, the chunk offsets come from shared memory, pass 2 writes.
 constexpr int PREFIX_WARPS = 16;
+
+// Compensated FP32 summation (Neumaier): s + c carries the running sum to about twice
+// FP32's precision, so the stored pair (s, c) differences keep FP32 relative accuracy even
+// for short row ranges of a long column. (FP64 arithmetic is much slower on this part.)
+__device__ __forceinline__ void comp_add(float &s, float &c, float v)
+{
+    const float t = s + v;
+    const bool s_big = fabsf(s) >= fabsf(v);
+    c += ((s_big ? s : v) - t) + (s_big ? v : s);
+    s = t;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(32 * PREFIX_WARPS)
 k_row_prefix(GeomDev G, const T *__restrict__ g, float2 *__restrict__ ps, int prescale)
 {
-    __shared__ double s_tot[PREFIX_WARPS][32];
+    __shared__ float2 s_tot[PREFIX_WARPS][32];
     const int lane = threadIdx.x, w = threadIdx.y;
     const int k = blockIdx.y, iu = blockIdx.x * 32 + lane;
     const bool ok = iu < G.nu;
@@ -320,26 +331,29 @@ k_row_prefix(GeomDev G, const T *__restrict__ g, float2 *__restrict__ ps, int pr
         dyr = r4.y;
     }
     const T *src = g + (size_t)k * G.nv * G.nu + iu;
-    double t = 0.0;
+    float ts = 0.0f, tc = 0.0f;
     if (ok)
         for (int iv = r0; iv < r1; ++iv) {
             float val = load_as_float(src + (size_t)iv * G.nu);
             if (prescale) val *= ray_length(dxr, dyr, imager_v(G, iv));
-            t += (double)val;
+            comp_add(ts, tc, val);
         }
-    s_tot[w][lane] = t;
+    s_tot[w][lane] = make_float2(ts, tc);
     __syncthreads();
-    double run = 0.0;
-    for (int c = 0; c < w; ++c) run += s_tot[c][lane];
+    float rs = 0.0f, rc = 0.0f; // the chunks before this warp's
+    for (int c = 0; c < w; ++c) {
+        const float2 t = s_tot[c][lane];
+        comp_add(rs, rc, t.x);
+        rc += t.y;
+    }
     if (!ok) return;
     float2 *dst = ps + (size_t)k * ((size_t)G.nv + 1) * G.nu + iu; // prefix m at dst[m * nu]
     if (w == 0) dst[0] = make_float2(0.0f, 0.0f);
     for (int iv = r0; iv < r1; ++iv) {
         float val = load_as_float(src + (size_t)iv * G.nu);
         if (prescale) val *= ray_length(dxr, dyr, imager_v(G, iv));
-        run += (double)val;
-        const float hi = (float)run;
-        dst[(size_t)(iv + 1) * G.nu] = make_float2(hi, (float)(run - (double)hi));
+        comp_add(rs, rc, val);
+        dst[(size_t)(iv + 1) * G.nu] = make_float2(rs, rc);
     }
 }
 
