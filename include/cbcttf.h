@@ -95,8 +95,11 @@ typedef struct {
  * Creates a geometry on the current CUDA device and copies the view table to it.
  * The whole volume must lie strictly between the source and the imager for every view
  * (its transverse half-diagonal below both sad and sdd - sad). Sizes are limited to
- * nx + ny <= 4096, nz <= 1024, nx*ny*nz < 2^31 voxels and n_views*nv*nu < 2^31 pixels.
- * Synchronous. Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA.
+ * nx + ny <= 4096, nz <= 1024, nx*ny*nz < 2^31 voxels and n_views*nv*nu < 2^31 pixels,
+ * and jointly by the projector's shared memory per block, about
+ * 20 (nx + ny) + 196 nz bytes <= 200 KiB (nz <= 933 at nx + ny = 1024, nz <= 618 at
+ * nx + ny = 4096); a larger grid gives UNSUPPORTED.
+ * Synchronous. Errors: INVALID_ARG, UNSUPPORTED, OUT_OF_MEMORY, CUDA.
  */
 cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct_geometry **out);
 

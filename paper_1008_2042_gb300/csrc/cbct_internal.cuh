@@ -185,6 +185,9 @@ int project_num_blocks(const GeomDev &G);
 // at least this much slack, and its base is 16-byte aligned.
 constexpr size_t PROJECT_VOLUME_SLACK = 64;
 
+// Dynamic shared memory a projector block may use (opted in per kernel).
+constexpr size_t PROJECT_SMEM_LIMIT = 200 * 1024;
+
 // out holds `storage`-typed values (PM_COUNT: none); y is FP32; sc supplies kappa in
 // PM_Q_SCALED. With FP32 storage the CGLS modes store |D - S| r and |D - S| q.
 cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long long sy,
@@ -239,6 +242,11 @@ cbct_status ensure_scratch(cbct_geometry *g, size_t bytes);
 // server): argument checks, the host view table (angles and FP32 cos/sin), and the
 // stream-ordered ray-table kernel.
 cbct_status validate_geometry_desc(const cbct_geometry_desc &d);
+// Shared memory one projector block needs on the finest grid (the largest level).
+size_t project_smem_bytes(const GeomDev &G);
+// UNSUPPORTED when the projector's per-block shared memory for this geometry exceeds what
+// it may use (its staged z-lines and tables grow with nz, its segment lists with nx + ny).
+cbct_status check_projector_fits(const cbct_geometry_desc &d);
 void view_table(const cbct_geometry_desc &d, double *angles, float2 *cs);
 cbct_status launch_ray_table(const cbct_geometry *g, cudaStream_t st);
 

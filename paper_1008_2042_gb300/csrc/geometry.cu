@@ -260,6 +260,19 @@ cbct_status validate_geometry_desc(const cbct_geometry_desc &d)
     return CBCT_OK;
 }
 
+cbct_status check_projector_fits(const cbct_geometry_desc &d)
+{
+    cbct_geometry tmp{};
+    tmp.desc = d;
+    const size_t need = project_smem_bytes(level_geom(&tmp, 0));
+    if (need > PROJECT_SMEM_LIMIT)
+        return set_error(CBCT_ERR_UNSUPPORTED,
+                         "geometry: the projector needs %zu bytes of shared memory per block for this grid "
+                         "(limit %zu): reduce nz or nx + ny",
+                         need, PROJECT_SMEM_LIMIT);
+    return CBCT_OK;
+}
+
 void view_table(const cbct_geometry_desc &d, double *angles, float2 *cs)
 {
     for (int k = 0; k < d.n_views; k++) {
@@ -288,6 +301,8 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct
     const cbct_geometry_desc &d = *desc;
     {
         cbct_status v = validate_geometry_desc(d);
+        if (v != CBCT_OK) return v;
+        v = check_projector_fits(d);
         if (v != CBCT_OK) return v;
     }
 

@@ -77,7 +77,7 @@ static inline size_t project_smem(const GeomDev &G, int sg);
 
 static inline int segment_group(const GeomDev &G)
 {
-    return project_smem(G, SEG_GROUP_MAX) <= 200 * 1024 ? SEG_GROUP_MAX : SEG_GROUP_MAX / 2;
+    return project_smem(G, SEG_GROUP_MAX) <= PROJECT_SMEM_LIMIT ? SEG_GROUP_MAX : SEG_GROUP_MAX / 2;
 }
 
 // Shared memory of one block: the two crossing lists, then (16-byte aligned) per segment
@@ -437,9 +437,9 @@ template <int MODE, typename TP, int SG> static std::atomic<unsigned long long> 
 
 template <int MODE, typename TP> static cbct_status project_optin()
 {
-    cudaError_t e = smem_optin_once(k_project<MODE, TP, SEG_GROUP_MAX>, 200 * 1024, g_project_optin<MODE, TP, SEG_GROUP_MAX>);
+    cudaError_t e = smem_optin_once(k_project<MODE, TP, SEG_GROUP_MAX>, (int)PROJECT_SMEM_LIMIT, g_project_optin<MODE, TP, SEG_GROUP_MAX>);
     if (e == cudaSuccess)
-        e = smem_optin_once(k_project<MODE, TP, SEG_GROUP_MAX / 2>, 200 * 1024, g_project_optin<MODE, TP, SEG_GROUP_MAX / 2>);
+        e = smem_optin_once(k_project<MODE, TP, SEG_GROUP_MAX / 2>, (int)PROJECT_SMEM_LIMIT, g_project_optin<MODE, TP, SEG_GROUP_MAX / 2>);
     return e == cudaSuccess ? CBCT_OK : check_cuda(e, "project attribute");
 }
 
@@ -485,7 +485,7 @@ cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long 
     dim3 grid((unsigned)(G.nviews * G.nu), (unsigned)((G.nv + 2 * threads - 1) / (2 * threads)));
     const int sg = segment_group(G);
     const size_t smem = project_smem(G, sg);
-    if (smem > 200 * 1024)
+    if (smem > PROJECT_SMEM_LIMIT)
         return set_error(CBCT_ERR_UNSUPPORTED, "project: grid too large for the projector's shared memory (nx + ny and nz)");
     if (sz != 1) return set_error(CBCT_ERR_INVALID_ARG, "project: the volume must be z-contiguous");
     const int isx = (int)sx, isy = (int)sy;

@@ -380,6 +380,7 @@ extern "C" cbct_status cbct_server_submit(cbct_server *srv, const cbct_geometry_
     if (!srv || !desc || !y_host || !f_host || !iters || !id)
         return set_error(CBCT_ERR_INVALID_ARG, "server_submit: null argument");
     SRV_TRY(validate_geometry_desc(*desc));
+    SRV_TRY(check_projector_fits(*desc));
     cbct_recon_opts o{3, 1, 1, CBCT_F32};
     if (opts) o = *opts;
     SRV_TRY(validate_recon_args(mu, lambda, levels, iters, o));

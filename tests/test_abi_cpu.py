@@ -62,6 +62,23 @@ def test_invalid_geometry_is_rejected_before_device_work(lib, bad):
     assert lib.cbct_last_error()
 
 
+@pytest.mark.parametrize("nx,ny,nz,ok", [(512, 512, 933, True), (512, 512, 934, False),
+                                         (64, 4032, 618, True), (64, 4032, 619, False)])
+def test_grids_beyond_the_projectors_shared_memory_are_unsupported(lib, nx, ny, nz, ok):
+    """Largest grids: accepted up to the projector's shared-memory limit, UNSUPPORTED past
+    it, before any device work (ok=True cases stop at the device allocation here)."""
+    d = _desc(nx=nx, ny=ny, nz=nz, dx=0.2, dy=0.2, dz=0.1)
+    h = ctypes.c_void_p()
+    st = lib.cbct_geometry_create(ctypes.byref(d), ctypes.byref(h))
+    if ok:
+        assert st != 5, lib.cbct_last_error()
+        if st == 0:
+            lib.cbct_geometry_destroy(h)
+    else:
+        assert st == 5
+        assert b"shared memory" in lib.cbct_last_error()
+
+
 def test_null_arguments_are_rejected(lib):
     assert lib.cbct_geometry_create(None, None) == 1
     assert lib.cbct_project(None, None, None, None) == 1

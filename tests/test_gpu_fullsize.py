@@ -1,0 +1,121 @@
+"""Parity of P and P^T at the paper-scale workload and at the largest grids the library
+accepts, on outputs the FP64 oracle evaluates one by one (sampled rays for P, sampled
+voxels for P^T), plus the adjoint identity at full size and degenerate shapes.
+
+The paper-scale case is the reconstruction benchmark's grid (512x512x70 voxels of
+0.5x0.5x2.5 mm, 512x384 imager at 0.776 mm, 40 views) on each of its multigrid levels, so
+every launch shape the benchmark times (group size, rows per block, z chunk) is covered.
+Bars: relative L2 over the samples <= 1e-4, and per sample |gpu - ref| <= tol |ref| +
+floor max|ref| (the floor covers short corner rays and rarely seen voxels, whose values are
+tiny) with tol = 1e-4 and floor = 1e-5 at the paper scale. On the largest grids the bars
+follow from FP32 ray parameters: transverse coordinates up to ~400 mm carry an absolute
+error of ~2.4e-5 mm against voxels of 0.2 mm, ~1e-4 of a chord, so there tol = 2e-3 and
+floor = 1e-4, and the widest grid (which fits the imager only with 0.2 mm voxels) has a
+relative-L2 bar of 3e-4.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cb():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1008_2042_gb300 import build
+    build.build()
+    import paper_1008_2042_gb300 as m
+    m.load_library()
+    return m
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float32, device="cuda")
+
+
+def check_samples(what, got, ref, per_sample, l2_bar, floor_rel):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    err = np.abs(got - ref)
+    floor = floor_rel * np.abs(ref).max()
+    worst = float(np.max(np.maximum(err - floor, 0.0) / np.maximum(np.abs(ref), 1e-30)))
+    l2 = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    print(f"\n{what}: worst sample beyond the floor {worst:.2e}, relative L2 over samples {l2:.2e}")
+    assert l2 <= l2_bar, (what, l2)
+    assert worst <= per_sample, (what, worst)
+
+
+def sampled_parity(cb, geom, seed, n_rays=2000, n_vox=200, per_sample=1e-4, l2_bar=1e-4, floor_rel=1e-5):
+    rng = np.random.default_rng(seed)
+    f = synth.random_volume(geom, seed, 0.0, 0.04)
+    y = synth.random_projections(geom, seed + 1, 0.0, 3.0)
+    with cb.Geometry(geom) as g:
+        p = cb.project(g, dev(f)).cpu().numpy().ravel()
+        b = cb.backproject(g, dev(y)).cpu().numpy().ravel()
+    rays = rng.choice(p.size, min(n_rays, p.size), replace=False)
+    check_samples("P", p[rays], oracle.project_rays(geom, f, rays), per_sample, l2_bar, floor_rel)
+    vox = rng.choice(b.size, min(n_vox, b.size), replace=False)
+    check_samples("P^T", b[vox], oracle.backproject_voxels(geom, y, vox), per_sample, l2_bar, floor_rel)
+
+
+@pytest.mark.parametrize("level", [0, 1, 2])
+def test_paper_scale_sampled_parity(cb, level):
+    sampled_parity(cb, synth.config_paper(40).level(level), 800 + level)
+
+
+def test_paper_scale_adjoint_identity(cb):
+    geom = synth.config_paper(40)
+    f = dev(synth.random_volume(geom, 810, 0.0, 0.04))
+    y = dev(synth.random_projections(geom, 811, 0.0, 3.0))
+    with cb.Geometry(geom) as g:
+        lhs = torch.dot(cb.project(g, f).double().ravel(), y.double().ravel()).item()
+        rhs = torch.dot(f.double().ravel(), cb.backproject(g, y).double().ravel()).item()
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+LARGEST = {
+    # nz at the projector's shared-memory limit for nx + ny = 512 (16-column groups)
+    "tall": synth.Geometry(nx=256, ny=256, nz=960, dx=1.0, dy=1.0, dz=0.2, nu=384, nv=200, du=1.5, dv=1.5,
+                           n_views=3, angles=(0.1, 1.7, 4.0)),
+    # nx + ny at its limit (4096): the longest transverse traces
+    "wide": synth.Geometry(nx=64, ny=4032, nz=16, dx=0.2, dy=0.2, dz=1.0, nu=600, nv=24, du=1.6, dv=1.5,
+                           n_views=3, angles=(0.05, 1.6, 3.3)),
+}
+
+
+@pytest.mark.parametrize("name", list(LARGEST))
+def test_largest_grids_sampled_parity(cb, name):
+    sampled_parity(cb, LARGEST[name], 820 + len(name), n_rays=1500, n_vox=150, per_sample=2e-3,
+                   l2_bar=3e-4 if name == "wide" else 1e-4, floor_rel=1e-4)
+
+
+DEGENERATE = {
+    "one_slice": synth.Geometry(nx=20, ny=16, nz=1, dx=2.0, dy=2.0, dz=3.0, nu=30, nv=5, du=2.0, dv=2.0,
+                                n_views=4, angles=(0.2, 1.1, 2.9, 5.0)),
+    "one_view": synth.Geometry(nx=16, ny=16, nz=8, dx=2.0, dy=2.0, dz=2.0, nu=24, nv=12, du=2.0, dv=2.0,
+                               n_views=1, angles=(0.4,)),
+    # one pixel, off the central ray (a ray lying in a voxel plane is a measure-zero tie)
+    "one_pixel": synth.Geometry(nx=8, ny=8, nz=4, dx=2.0, dy=2.0, dz=2.0, nu=1, nv=1, du=5.0, dv=5.0,
+                                u_off=0.37, v_off=0.23, n_views=3, angles=(0.1, 2.0, 4.0)),
+    "one_row": synth.Geometry(nx=12, ny=10, nz=6, dx=2.0, dy=2.0, dz=2.0, nu=20, nv=1, du=2.0, dv=2.0,
+                              n_views=2, angles=(0.3, 2.3)),
+}
+
+
+@pytest.mark.parametrize("name", list(DEGENERATE))
+def test_degenerate_shapes_full_parity(cb, name):
+    geom = DEGENERATE[name]
+    f = synth.random_volume(geom, 830)
+    y = synth.random_projections(geom, 831)
+    with cb.Geometry(geom) as g:
+        p = cb.project(g, dev(f)).cpu().numpy()
+        b = cb.backproject(g, dev(y)).cpu().numpy()
+    pr, br = oracle.project(geom, f), oracle.backproject(geom, y)
+    assert np.linalg.norm(p - pr) <= 1e-4 * max(np.linalg.norm(pr), 1e-30)
+    assert np.linalg.norm(b - br) <= 1e-4 * max(np.linalg.norm(br), 1e-30)

@@ -187,3 +187,12 @@ def test_nonzero_count_matches_paper_order_of_magnitude():
                           n_views=K // 4, angles=tuple(2 * np.pi * np.arange(K // 4) / K))
     nnz = 4 * oracle.count_nnz(geom)
     assert 0.5 * g["nnz_clinical"][0] <= nnz <= 2.0 * g["nnz_clinical"][0], nnz
+
+
+def test_sampled_projection_matches_full_projection():
+    geom = synth.Geometry(nx=32, ny=24, nz=8, dx=2.0, dy=2.0, dz=3.0, nu=64, nv=16, du=1.6,
+                          dv=2.0, n_views=10)
+    f = synth.random_volume(geom, 9)
+    full = oracle.project(geom, f).ravel()
+    sel = np.random.default_rng(1).choice(full.size, 300, replace=False)
+    assert np.array_equal(oracle.project_rays(geom, f, sel), full[sel])
