@@ -73,6 +73,7 @@ def _load():
                 "o_tf_synthesize": (None, [ctypes.c_int] * 3 + [_P, _P]),
                 "o_tf_shrink": (None, [ctypes.c_int] * 3 + [_P, ctypes.c_double]),
                 "o_positivity": (None, [ctypes.c_long, _P]),
+                "o_tf_shrink_voxels": (None, [ctypes.c_int] * 3 + [_P, ctypes.c_double, ctypes.c_int, ctypes.c_long, _PL, _P]),
                 "o_cgls": (None, [G, _P, _P, ctypes.c_int, _P]),
                 "o_cgls_storage": (None, [G, _P, _P, ctypes.c_int, _P, ctypes.c_int]),
                 "o_round_storage": (None, [ctypes.c_long, _P, ctypes.c_int]),
@@ -222,6 +223,18 @@ def positivity(f):
     a = _f64(f).copy()
     lib.o_positivity(a.size, _ptr(a))
     return a
+
+
+def tf_shrink_voxels(f, mu, positive, voxels):
+    """H(W^T T_mu W f) at selected flat voxel indices (z*ny + y)*nx + x."""
+    lib = _load()
+    f = _f64(f)
+    nz, ny, nx = f.shape
+    voxels = np.ascontiguousarray(voxels, dtype=np.int64)
+    out = np.empty(voxels.shape[0])
+    lib.o_tf_shrink_voxels(nx, ny, nz, _ptr(f), float(mu), int(bool(positive)), voxels.shape[0],
+                           voxels.ctypes.data_as(_PL), _ptr(out))
+    return out
 
 
 def tf_synthesize_shrink(alpha, mu, positive):

@@ -549,6 +549,54 @@ void o_tf_shrink(int nx, int ny, int nz, double *alpha, double mu)
     }
 }
 
+/*
+ * The regularisation step H(W^T T_mu W f) at selected voxels only (flat index
+ * (z*ny + y)*nx + x), from the same three definitions as o_tf_analyze, o_tf_shrink and
+ * o_tf_synthesize: the output at x needs the shrunk coefficients at x + k for k in
+ * {-1,0,1}^3, each of which needs f on its own 3x3x3 neighbourhood (periodic). For sampled
+ * checks at full size. Pinned by: equality with the three whole-volume steps (tests).
+ */
+void o_tf_shrink_voxels(int nx, int ny, int nz, const double *f, double mu, int positivity, long nsel,
+                        const long *vox, double *out)
+{
+    double H[3][3];
+    tf_taps(H);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long s = 0; s < nsel; s++) {
+        const long j = vox[s];
+        const int x = (int)(j % nx), y = (int)((j / nx) % ny), z = (int)(j / ((long)nx * ny));
+        double acc = 0.0;
+        for (int c = -1; c <= 1; c++)
+            for (int b = -1; b <= 1; b++)
+                for (int a = -1; a <= 1; a++) {
+                    /* coefficients at p = x + (a, b, c) */
+                    const int px = wrap(x + a, nx), py = wrap(y + b, ny), pz = wrap(z + c, nz);
+                    double al[27];
+                    for (int i = 0; i < 27; i++) {
+                        int l = i % 3, m = (i / 3) % 3, nn = i / 9;
+                        double t = 0.0;
+                        for (int cc = -1; cc <= 1; cc++)
+                            for (int bb = -1; bb <= 1; bb++)
+                                for (int aa = -1; aa <= 1; aa++)
+                                    t += H[l][aa + 1] * H[m][bb + 1] * H[nn][cc + 1] *
+                                         f[((long)wrap(pz - cc, nz) * ny + wrap(py - bb, ny)) * nx + wrap(px - aa, nx)];
+                        al[i] = t;
+                    }
+                    double s2 = 0.0;
+                    for (int i = 1; i < 27; i++) s2 += al[i] * al[i];
+                    const double nrm = sqrt(s2);
+                    const double scale = nrm > mu ? 1.0 - mu / nrm : 0.0;
+                    for (int i = 1; i < 27; i++) al[i] *= scale;
+                    /* synthesis: psi_i(k) alpha_i(x + k) with k = (a, b, c) */
+                    for (int i = 0; i < 27; i++) {
+                        int l = i % 3, m = (i / 3) % 3, nn = i / 9;
+                        acc += H[l][a + 1] * H[m][b + 1] * H[nn][c + 1] * al[i];
+                    }
+                }
+        out[s] = (positivity && acc < 0.0) ? 0.0 : acc;
+    }
+}
+
 /* Positivity correction H (Section 2.1): negative voxels set to zero (NaN passes). */
 void o_positivity(long n, double *f)
 {

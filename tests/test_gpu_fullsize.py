@@ -119,3 +119,31 @@ def test_degenerate_shapes_full_parity(cb, name):
     pr, br = oracle.project(geom, f), oracle.backproject(geom, y)
     assert np.linalg.norm(p - pr) <= 1e-4 * max(np.linalg.norm(pr), 1e-30)
     assert np.linalg.norm(b - br) <= 1e-4 * max(np.linalg.norm(br), 1e-30)
+
+
+@pytest.mark.parametrize("layout", ["public", "iteration"])
+def test_paper_scale_regularisation_step_sampled(cb, layout):
+    """The fused H(W^T T_mu W f) on the 512x512x70 volume, in the public x-fastest layout and
+    in the iteration's z-fastest layout (the launch shape the reconstruction uses; the step
+    does not depend on the axis order), against the oracle at sampled voxels."""
+    geom = synth.config_paper(40)
+    f = synth.random_volume(geom, 840, 0.0, 0.04)
+    mu = 5e-4
+    if layout == "public":
+        out = cb.tf_shrink(dev(f), mu, True).cpu().numpy()
+    else:
+        fz = np.ascontiguousarray(f.transpose(1, 2, 0))  # (ny, nx, nz): z fastest
+        out = cb.tf_shrink(dev(fz), mu, True).cpu().numpy().transpose(2, 0, 1)
+    sel = np.random.default_rng(841).choice(f.size, 1000, replace=False)
+    got = out.ravel()[sel]
+    ref = oracle.tf_shrink_voxels(f, mu, True, sel)
+    pre = oracle.tf_shrink_voxels(f, mu, False, sel)  # H is 1-Lipschitz: measure before it
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(pre), np.linalg.norm(got - ref) / np.linalg.norm(pre)
+
+
+def test_paper_scale_frame_round_trip(cb):
+    """W^T W = I at full size: analysis then synthesis without shrinkage or positivity."""
+    geom = synth.config_paper(40)
+    f = dev(synth.random_volume(geom, 842, 0.0, 0.04))
+    back = cb.tf_synthesize_shrink(cb.tf_analyze(f), 0.0, False)
+    assert (torch.linalg.norm(back - f) / torch.linalg.norm(f)).item() <= 1e-6

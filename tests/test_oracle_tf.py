@@ -117,3 +117,13 @@ def test_vector_shrinkage_formula():
 def test_positivity():
     f = np.array([-1.0, 0.0, 2.0, -1e-300])
     assert np.array_equal(oracle.positivity(f), np.array([0.0, 0.0, 2.0, 0.0]))
+
+
+def test_sampled_regularisation_step_matches_the_three_steps():
+    f = np.random.default_rng(21).standard_normal((6, 9, 11))
+    alpha = oracle.tf_analyze(f)
+    mu = float(np.median(np.sqrt((alpha[1:] ** 2).sum(0))))
+    for positive in (False, True):
+        full = oracle.tf_synthesize_shrink(alpha, mu, positive).ravel()
+        sel = np.arange(full.size)
+        assert np.abs(oracle.tf_shrink_voxels(f, mu, positive, sel) - full).max() <= 1e-12 * np.abs(full).max()
