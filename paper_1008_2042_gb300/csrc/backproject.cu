@@ -21,15 +21,12 @@
 namespace cbct {
 
 constexpr int BP_TX = 32, BP_TY = 4;
-#ifndef CBCT_BP_MAX_ZC
-#define CBCT_BP_MAX_ZC 8 // z voxels per thread at most (8 or 16)
-#endif
 
 static int bp_zchunk(const GeomDev &G)
 {
     const long long tiles = (long long)((G.nx + BP_TX - 1) / BP_TX) * ((G.ny + BP_TY - 1) / BP_TY);
     const long long want = 4LL * device_sm_count();
-    int zc = CBCT_BP_MAX_ZC;
+    int zc = 8; // z voxels per thread at most
     while (zc > 1 && tiles * ((G.nz + zc - 1) / zc) < want) zc >>= 1;
     return zc;
 }
@@ -99,7 +96,7 @@ __device__ __forceinline__ void plane_terms_inside(const GeomDev &G, const float
     above = g * (up ? whi : wlo);
 }
 
-template <int ZC>
+template <int ZC, bool FLAT>
 __global__ void __launch_bounds__(BP_TX *BP_TY)
 k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out, int sx, int sy, int sz,
               float *__restrict__ out2, double *__restrict__ partials)
@@ -135,9 +132,9 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
         const size_t view_stride = ((size_t)G.nv + 1) * G.nu;
         const float c0 = fmaf(-G.v_first, G.inv_dv, -1e-3f), c1 = fmaf(-G.v_first, G.inv_dv, 1e-3f);
 
-        for (int k = 0; k < G.nviews; ++k) {
+        // imager columns in the shadow of the voxel column in view k (its corners' u)
+        auto shadow = [&](int k, int &lo, int &hi) {
             const float2 cs = G.cs[k];
-            // shadow of the column on the imager: u of its four corners
             float umin = 3.0e38f, umax = -3.0e38f;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -148,17 +145,18 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
                 umin = fminf(umin, u);
                 umax = fmaxf(umax, u);
             }
-            const int iu_lo = max(0, (int)ceilf(fmaf(umin - G.u_first, G.inv_du, -1e-3f)));
-            const int iu_hi = min(G.nu - 1, (int)floorf(fmaf(umax - G.u_first, G.inv_du, 1e-3f)));
-
-            for (int iu = iu_lo; iu <= iu_hi; ++iu) {
+            lo = max(0, (int)ceilf(fmaf(umin - G.u_first, G.inv_du, -1e-3f)));
+            hi = min(G.nu - 1, (int)floorf(fmaf(umax - G.u_first, G.inv_du, 1e-3f)));
+        };
+        // all rows of imager column iu in view k that cross this voxel column
+        auto visit = [&](int k, int iu) {
                 const float4 r4 = __ldg(G.ray4 + k * G.nu + iu); // (dxr, dyr, qx, qy)
                 const float2 r2 = __ldg(G.ray2 + k * G.nu + iu); // (1/dxr, 1/dyr)
                 const float t0 = tau_plane(xl, r4.z, r2.x), t1 = tau_plane(xh, r4.z, r2.x);
                 const float t2 = tau_plane(yl, r4.w, r2.y), t3 = tau_plane(yh, r4.w, r2.y);
                 const float ta = fmaxf(fminf(t0, t1), fminf(t2, t3));
                 const float tb = fminf(fmaxf(t0, t1), fmaxf(t2, t3));
-                if (!(tb > ta)) continue;
+                if (!(tb > ta)) return;
                 const float A = __fdividef(1.0f, G.tc + ta), B = __fdividef(1.0f, G.tc + tb);
                 const float wfull = tb - ta;
                 const float2 *col = ps + (size_t)k * view_stride + iu; // prefix m at col[m * nu]
@@ -240,6 +238,23 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
                         hi_p = hi_n;
                     }
                 }
+        };
+        if (FLAT) {
+            // Each lane walks its own list of candidates (view, imager column) across all
+            // views in one loop, so a warp runs for the longest per-lane total instead of the
+            // widest shadow in every view: fewer idle lanes where shadows are ~1 column wide.
+            int k = -1, iu = 0, iu_hi = -1;
+            for (;;) {
+                while (iu > iu_hi && k < G.nviews) // next view with a non-empty shadow
+                    if (++k < G.nviews) shadow(k, iu, iu_hi);
+                if (k >= G.nviews) break;
+                visit(k, iu++);
+            }
+        } else {
+            for (int k = 0; k < G.nviews; ++k) {
+                int lo, hi;
+                shadow(k, lo, hi);
+                for (int iu = lo; iu <= hi; ++iu) visit(k, iu);
             }
         }
     }
@@ -279,15 +294,19 @@ cbct_status launch_backproject(const GeomDev &G, const float2 *ps, float *out, l
     const size_t smem = sizeof(float) * G.nv;
     const int isx = (int)sx, isy = (int)sy, isz = (int)sz;
     ProfToken tok = prof_start(CBCT_KERNEL_BACKPROJECT, st);
+    // flatten the candidate loop where a voxel column's shadow spans about one imager
+    // column (its diagonal, magnified at the rotation axis, below 1.5 pixels)
+    const bool flat = sqrtf(G.dx * G.dx + G.dy * G.dy) * (G.sdd / G.sad) < 1.5f * G.du;
+#define CBCT_BP_LAUNCH(Z)                                                                                 \
+    if (flat) k_backproject<Z, true><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials); \
+    else k_backproject<Z, false><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials)
     switch (zc) {
-#if CBCT_BP_MAX_ZC >= 16
-    case 16: k_backproject<16><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials); break;
-#endif
-    case 8: k_backproject<8><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials); break;
-    case 4: k_backproject<4><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials); break;
-    case 2: k_backproject<2><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials); break;
-    default: k_backproject<1><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials); break;
+    case 8: CBCT_BP_LAUNCH(8); break;
+    case 4: CBCT_BP_LAUNCH(4); break;
+    case 2: CBCT_BP_LAUNCH(2); break;
+    default: CBCT_BP_LAUNCH(1); break;
     }
+#undef CBCT_BP_LAUNCH
     prof_stop(tok, st);
     note_launch();
     return check_cuda(cudaGetLastError(), "backproject launch");
