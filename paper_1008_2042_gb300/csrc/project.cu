@@ -15,6 +15,7 @@
 // Accumulation is FP32; the epilogue can
 // scale by |D - S|, form the CGLS residual and reduce squared norms in FP64 into one
 // partial per block; the output is stored as FP32, BF16 or FP16.
+#include <atomic>
 #include <cfloat>
 
 #include "cbct_internal.cuh"
@@ -68,9 +69,10 @@ __device__ __forceinline__ int upper_count(const float *a, int n, float t) // # 
     return lo;
 }
 
+// segments of a trace (at most nx + ny + 1), padded to whole groups
 static inline int seg_capacity(const GeomDev &G, int sg)
 {
-    return ((G.nx + G.ny + 3 + sg - 1) / sg + 1) * sg;
+    return ((G.nx + G.ny + 2 + sg - 1) / sg) * sg;
 }
 
 static inline size_t project_smem(const GeomDev &G, int sg);
@@ -92,12 +94,19 @@ static inline int seg_offset(const GeomDev &G) { return ((G.nx + G.ny + 2 + 3) /
 // projector reads has at least 16 bytes of slack after it (PROJECT_VOLUME_SLACK).
 static inline int line_pitch(int nz) { return ((nz + 6 + 3) / 4) * 4; }
 
-// shared memory: crossing lists, per segment (end tau, column offset, (line offset,
-// length)), two staged groups of z-lines and the group's per-slab prefix table
+// shared memory: per segment (end tau, column offset, (line offset, length)); then two
+// staged groups of z-lines, whose space first holds phase 1's crossing lists; then the
+// group's per-slab prefix table
+static inline size_t line_region(const GeomDev &G, int sg)
+{
+    const size_t lines = 2 * (size_t)sg * line_pitch(G.nz), lists = (size_t)seg_offset(G);
+    return lines > lists ? lines : lists;
+}
+
 static inline size_t project_smem(const GeomDev &G, int sg)
 {
-    return sizeof(float) * (size_t)seg_offset(G) + (sizeof(float) + sizeof(int) + sizeof(float2)) * (size_t)seg_capacity(G, sg) +
-           sizeof(float) * (2 * (size_t)sg * line_pitch(G.nz) + (size_t)G.nz * (sg + 1));
+    return (sizeof(float) + sizeof(int) + sizeof(float2)) * (size_t)seg_capacity(G, sg) +
+           sizeof(float) * (line_region(G, sg) + (size_t)G.nz * (sg + 1));
 }
 
 size_t project_smem_bytes(const GeomDev &G) { return project_smem(G, segment_group(G)); }
@@ -129,17 +138,18 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
 {
     extern __shared__ __align__(16) float smem[];
     __shared__ double s_warp[PROJ_THREADS / 32];
-    float *sA = smem;                      // x-plane crossings, in ray order
-    float *sB = sA + (G.nx + 1);           // y-plane crossings
-    const int cap = ((G.nx + G.ny + 3 + SG - 1) / SG + 1) * SG;
-    float *sEnd = smem + ((G.nx + G.ny + 2 + 3) / 4) * 4; // tau at which segment j ends
+    const int cap = ((G.nx + G.ny + 2 + SG - 1) / SG) * SG;
+    float *sEnd = smem;                                    // tau at which segment j ends
     int *sCol = reinterpret_cast<int *>(sEnd + cap);      // voxel-column offset of segment j
     float2 *sSeg = reinterpret_cast<float2 *>(sCol + cap); // (line offset bits, length) of segment j
     const int pitch = ((G.nz + 6 + 3) / 4) * 4;            // floats per staged line
     const int quads = pitch / 4;                           // 16-byte pieces per line slot
     float *sLine = reinterpret_cast<float *>(sSeg + cap);  // two staged groups of z-lines
-    constexpr int TPITCH = SG + 1;
-    float *sTab = sLine + 2 * SG * pitch;                  // [nz][SG + 1] per-slab prefix table
+    float *sA = sLine;                                     // phase 1: x-plane crossings, in ray order
+    float *sB = sA + (G.nx + 1);                           // phase 1: y-plane crossings
+    const int lregion = max(2 * SG * pitch, ((G.nx + G.ny + 2 + 3) / 4) * 4);
+    constexpr int TPITCH = SG + 1;                         // odd: the build's threads (slabs) hit distinct banks
+    float *sTab = sLine + lregion;                         // [nz][SG + 1] per-slab prefix table
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int view = blockIdx.x / G.nu;
