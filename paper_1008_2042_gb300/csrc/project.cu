@@ -96,7 +96,7 @@ static inline int line_pitch(int nz) { return ((nz + 6 + 3) / 4) * 4; }
 
 // shared memory: per segment (end tau, column offset, (line offset, length)); then two
 // staged groups of z-lines, whose space first holds phase 1's crossing lists; then the
-// group's per-slab prefix table
+// group's per-slab prefix table and two rows of running per-slab totals
 static inline size_t line_region(const GeomDev &G, int sg)
 {
     const size_t lines = 2 * (size_t)sg * line_pitch(G.nz), lists = (size_t)seg_offset(G);
@@ -106,7 +106,7 @@ static inline size_t line_region(const GeomDev &G, int sg)
 static inline size_t project_smem(const GeomDev &G, int sg)
 {
     return (sizeof(float) + sizeof(int) + sizeof(float2)) * (size_t)seg_capacity(G, sg) +
-           sizeof(float) * (line_region(G, sg) + (size_t)G.nz * (sg + 1));
+           sizeof(float) * (line_region(G, sg) + (size_t)G.nz * (sg + 1) + 2 * (size_t)G.nz);
 }
 
 size_t project_smem_bytes(const GeomDev &G) { return project_smem(G, segment_group(G)); }
@@ -150,6 +150,7 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
     const int lregion = max(2 * SG * pitch, ((G.nx + G.ny + 2 + 3) / 4) * 4);
     constexpr int TPITCH = SG + 1;                         // odd: the build's threads (slabs) hit distinct banks
     float *sTab = sLine + lregion;                         // [nz][SG + 1] per-slab prefix table
+    float *sBase = sTab + G.nz * TPITCH;                   // [2][nz] running per-slab totals
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int view = blockIdx.x / G.nu;
@@ -315,6 +316,8 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
             const float *trow = sTab + k * TPITCH;
             return split && u > SG / 2 ? trow[u] + trow[SG / 2] : trow[u];
         };
+        float E[R] = {0.0f, 0.0f}; // running total where each row's current run starts
+        for (int k = tid; k < G.nz; k += nthr) sBase[k] = 0.0f; // published by the first barrier
         fill(0, 0);
         float g0 = tau_in;
         for (int ch = 0; ch < nchunk; ++ch) {
@@ -359,12 +362,20 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
             }
             __syncthreads();
             const float gend = sEnd[j + SG - 1];
+            // running per-slab totals: C[k][j + u] = base[k] + T[k][u] is the sum over all
+            // columns of the trace before column j + u; one thread per slab carries it on
+            const float *bcur = sBase + (ch & 1) * G.nz;
+            float *bnext = sBase + ((ch + 1) & 1) * G.nz;
+            for (int k = tid; k < G.nz; k += nthr) bnext[k] = bcur[k] + tab(k, SG);
+            // A row does nothing in a group it crosses no z plane in. At a crossing it adds
+            // its run in the slab it leaves (a difference of running totals, plus the part
+            // of the crossing column before the plane) and books the rest of that column to
+            // the slab it enters; E remembers the running total where that slab's run of
+            // whole columns starts.
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 float a = acc[r];
-                int first = 0;      // first column of the group not yet accounted
-                int cpend = -1;     // column whose remainder from tlast on is the current slab's
-                float tlast = 0.0f;
+                int cpend = -1; // column of this row's previous crossing in this group
                 while (tzn[r] < gend) { // a z crossing inside this group (the row is active)
                     const float t = tzn[r];
                     // The segment holding the crossing: the x and y planes the ray has passed
@@ -376,32 +387,33 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
                     na = min(max(sxs > 0 ? na : -na, 0), nA);
                     nb = min(max(sys > 0 ? nb : -nb, 0), nB);
                     const int c = min(max(na + nb - j, max(cpend, 0)), SG - 1);
-                    const float fcur = lines[__float_as_int(sSeg[j + c].x) + kz[r]];
-                    if (c == cpend) {
-                        a = fmaf(fcur, t - tlast, a);
-                    } else {
-                        if (cpend >= 0)
-                            a = fmaf(lines[__float_as_int(sSeg[j + cpend].x) + kz[r]], sEnd[j + cpend] - tlast, a);
-                        a += tab(kz[r], c) - tab(kz[r], first);
-                        a = fmaf(fcur, fmaxf(t - (c ? sEnd[j + c - 1] : g0), 0.0f), a);
-                    }
+                    const int lo = __float_as_int(sSeg[j + c].x);
+                    const float en = sEnd[j + c];
+                    const float fcur = lines[lo + kz[r]];
+                    if (c == cpend) // entered this slab in this same column: trim the booked rest
+                        a = fmaf(-fcur, en - t, a);
+                    else
+                        a += (bcur[kz[r]] + tab(kz[r], c)) - E[r] +
+                             fcur * fmaxf(t - (c ? sEnd[j + c - 1] : g0), 0.0f);
                     cpend = c;
-                    tlast = t;
-                    first = c + 1;
                     kz[r] += skz[r];
                     active[r] = (unsigned)kz[r] < (unsigned)G.nz;
+                    if (active[r]) {
+                        a = fmaf(lines[lo + kz[r]], en - t, a);
+                        E[r] = bcur[kz[r]] + tab(kz[r], c + 1);
+                    }
                     tzn[r] = active[r] ? tau_zplane(plane_at(kz[r] + (skz[r] > 0), G.dz, G.z0), inv_v[r], G.tc) : P_INF;
-                }
-                if (active[r]) {
-                    if (cpend >= 0)
-                        a = fmaf(lines[__float_as_int(sSeg[j + cpend].x) + kz[r]], sEnd[j + cpend] - tlast, a);
-                    a += tab(kz[r], SG) - tab(kz[r], first);
                 }
                 acc[r] = a;
             }
             g0 = gend;
             __syncthreads();
         }
+        // the run each still-active row ends in: up to the end of the trace
+        const float *bend = sBase + (nchunk & 1) * G.nz;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (active[r]) acc[r] += bend[kz[r]] - E[r];
     }
 
     // ---- epilogue ----
