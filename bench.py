@@ -187,13 +187,14 @@ class ClockSampler:
 
 
 def kernel_sources_sha(kernel: str) -> str:
-    """sha256 over the CUDA sources that define a kernel (its .cu file and the internal
+    """sha256 over the CUDA sources that define a kernel (its source files and the internal
     header), to tie a stored ncu traffic figure to the kernel version it was taken on."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1008_2042_gb300", "csrc")
-    files = {"k_project": "project.cu", "k_backproject": "backproject.cu"}[kernel]
+    files = {"k_project": ("project.cu", "project.cuh", "project_kernel.cuh"),
+             "k_backproject": ("backproject.cu",)}[kernel]
     h = hashlib.sha256()
-    for name in (files, "cbct_internal.cuh"):
+    for name in files + ("cbct_internal.cuh",):
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()

@@ -379,6 +379,22 @@ cbct_status cbct_server_stats_get(cbct_server *srv, cbct_server_stats *stats);
 /* Finishes every queued and admitted request, stops the worker and frees the server. */
 cbct_status cbct_server_destroy(cbct_server *srv);
 
+/*
+ * Column groups of the projector (tuning and testing; not part of the paper's method).
+ * Along each ray's transverse trace (Section 2.2.1's Siddon walk) the projector stages the
+ * voxel columns in groups of 16, 24, 32, 40, 48, 56, 64, 80 or 96 and, by default, gives
+ * each launch the largest group that keeps the most blocks resident per SM. Results of
+ * different group sizes agree to FP32 rounding (the sums are associated differently).
+ *
+ * cbct_set_project_group: process-wide; 0 restores the automatic choice, one of the sizes
+ * above forces it for every launch whose shared memory it fits (larger grids keep the
+ * automatic choice). Any other value returns CBCT_ERR_INVALID_ARG and changes nothing.
+ * cbct_project_group: the group size an FP32 projection of multigrid level `level` of `g`
+ * uses on the current device, in *segments.
+ */
+cbct_status cbct_set_project_group(int segments);
+cbct_status cbct_project_group(const cbct_geometry *g, int level, int *segments);
+
 /* Kernel families reported by cbct_kernel_time. */
 typedef enum {
     CBCT_KERNEL_PROJECT = 0,     /* the projector P */

@@ -94,6 +94,8 @@ _SIGNATURES = {
     "cbct_prolong": [_i, _i, _i, _d, _d, _d, _vp, _i, _i, _i, _d, _d, _d, _vp, _vp],
     "cbct_restrict": [_i, _i, _i, _d, _d, _d, _vp, _i, _i, _i, _d, _d, _d, _vp, _vp],
     "cbct_count_nnz": [_vp, _i, ctypes.POINTER(ctypes.c_ulonglong), _vp],
+    "cbct_set_project_group": [_i],
+    "cbct_project_group": [_vp, _i, ctypes.POINTER(ctypes.c_int)],
     "cbct_server_create": [ctypes.c_void_p, ctypes.POINTER(_vp)],
     "cbct_server_submit": [_vp, ctypes.POINTER(GeometryDesc), _vp, _f, _f, _i, ctypes.POINTER(_i),
                            ctypes.POINTER(ReconOpts), _vp, ctypes.POINTER(ctypes.c_longlong)],
@@ -410,6 +412,22 @@ def count_nnz(geom: Geometry, level: int = 0, stream=None) -> int:
     """Non-zeros of P on a multigrid level, counted by the projector itself."""
     n = ctypes.c_ulonglong()
     _check(load_library().cbct_count_nnz(geom.handle, int(level), ctypes.byref(n), _stream(stream)))
+    return int(n.value)
+
+
+PROJECT_GROUP_SIZES = (16, 24, 32, 40, 48, 56, 64, 80, 96)
+
+
+def set_project_group(segments: int) -> None:
+    """Force the projector's column-group size (one of PROJECT_GROUP_SIZES); 0 restores
+    the automatic per-launch choice. Process-wide."""
+    _check(load_library().cbct_set_project_group(int(segments)))
+
+
+def project_group(geom: Geometry, level: int = 0) -> int:
+    """The column-group size an FP32 projection of `level` uses on the current device."""
+    n = ctypes.c_int()
+    _check(load_library().cbct_project_group(geom.handle, int(level), ctypes.byref(n)))
     return int(n.value)
 
 

@@ -12,7 +12,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcbcttf.so")
-SOURCES = ["geometry.cu", "project.cu", "backproject.cu", "tf.cu", "recon.cu", "project_static.cu", "serve.cu"]
+SOURCES = ["geometry.cu", "project.cu", "project_groups_16_32.cu", "project_groups_40_56.cu",
+           "project_groups_64_96.cu", "backproject.cu", "tf.cu", "recon.cu", "project_static.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
@@ -36,7 +37,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     """Compile every CUDA source and link the shared library; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    headers = [os.path.join(CSRC, "cbct_internal.cuh"), os.path.join(ROOT, "include", "cbcttf.h")]
+    headers = [os.path.join(CSRC, h) for h in ("cbct_internal.cuh", "project.cuh", "project_kernel.cuh")]
+    headers.append(os.path.join(ROOT, "include", "cbcttf.h"))
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

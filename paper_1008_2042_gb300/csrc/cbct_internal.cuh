@@ -244,6 +244,10 @@ cbct_status ensure_scratch(cbct_geometry *g, size_t bytes);
 cbct_status validate_geometry_desc(const cbct_geometry_desc &d);
 // Shared memory one projector block needs on the finest grid (the largest level).
 size_t project_smem_bytes(const GeomDev &G);
+// Force the projector's column-group size (0: choose per launch); the size a PM_PLAIN FP32
+// launch on G uses.
+cbct_status project_set_group(int sg);
+cbct_status project_group_of(const GeomDev &G, int *sg);
 // UNSUPPORTED when the projector's per-block shared memory for this geometry exceeds what
 // it may use (its staged z-lines and tables grow with nz, its segment lists with nx + ny).
 cbct_status check_projector_fits(const cbct_geometry_desc &d);

@@ -360,6 +360,20 @@ extern "C" cbct_status cbct_geometry_destroy(cbct_geometry *g)
     return check_cuda(e, "geometry_destroy");
 }
 
+extern "C" cbct_status cbct_set_project_group(int segments)
+{
+    g_last_error[0] = '\0';
+    return project_set_group(segments);
+}
+
+extern "C" cbct_status cbct_project_group(const cbct_geometry *gc, int level, int *segments)
+{
+    g_last_error[0] = '\0';
+    if (!gc || !segments) return set_error(CBCT_ERR_INVALID_ARG, "project_group: null argument");
+    if (level < 0 || level > 16) return set_error(CBCT_ERR_INVALID_ARG, "project_group: bad level");
+    return project_group_of(level_geom(const_cast<cbct_geometry *>(gc), level), segments);
+}
+
 // Non-zeros of P: the projector run in counting mode, one partial per block, summed on
 // the host in block order.
 extern "C" cbct_status cbct_count_nnz(const cbct_geometry *gc, int level, unsigned long long *nnz,

@@ -1,41 +1,14 @@
-// Forward projector P (Eq. (1), Section 2.2.1: one ray per imager pixel, Siddon's exact
-// ray tracing, g_i = sum_j a_ij f_j with a_ij the length of ray i inside voxel j).
-//
-// GB300 mapping. All rays of one view that hit the same imager column u share their
-// transverse path through the (x, y) voxel columns; the imager row v only tilts them in
-// z. A block owns one (view, column) pair and its threads own the imager rows. The
-// block first computes the shared transverse Siddon trace once, cooperatively, into
-// shared memory (a parallel merge of the x-plane and y-plane crossing lists). Along that
-// trace a ray of row v stays in one z slab for long runs of columns (the cone is narrow),
-// and the block holds more rows than the volume has slabs. So, group by group of
-// columns, the block stages the columns' z-lines (contiguous in the iteration's
-// z-fastest layout) and forms per slab the running sum of voxel value x segment length;
-// a row's line integral over a run of columns in one slab is then the difference of two
-// table entries, and only the columns where it crosses a z plane are split explicitly.
-// Accumulation is FP32; the epilogue can
-// scale by |D - S|, form the CGLS residual and reduce squared norms in FP64 into one
-// partial per block; the output is stored as FP32, BF16 or FP16.
+// Forward projector P (Eq. (1), Section 2.2.1): host dispatcher. Chooses the column-group
+// size of each launch, opts the kernel into its shared memory and launches it. The kernel
+// itself is in project_kernel.cuh.
 #include <atomic>
-#include <cfloat>
+#include <map>
+#include <mutex>
+#include <tuple>
 
-#include "cbct_internal.cuh"
+#include "project.cuh"
 
 namespace cbct {
-
-constexpr int PROJ_THREADS = 192; // threads per block; each thread walks two imager rows
-#ifndef CBCT_PROJ_MIN_BLOCKS
-#define CBCT_PROJ_MIN_BLOCKS 4 // resident blocks per SM the register budget is sized for
-#endif
-constexpr float P_INF = 3.0e38f;
-
-// threads of a block (a multiple of 32, every lane present for warp votes) and the imager
-// rows one block covers (two per thread)
-static inline int proj_threads(const GeomDev &G)
-{
-    const int rows = G.nv < 2 * PROJ_THREADS ? G.nv : 2 * PROJ_THREADS;
-    const int t = (((rows + 1) / 2 + 31) / 32) * 32;
-    return t < PROJ_THREADS ? t : PROJ_THREADS;
-}
 
 int project_num_blocks(const GeomDev &G)
 {
@@ -43,460 +16,126 @@ int project_num_blocks(const GeomDev &G)
     return G.nviews * G.nu * ((G.nv + rows - 1) / rows);
 }
 
-// Column segments per group (one staged set of z-lines and one prefix table): 32, or 16
-// where the shared memory of 32 would not fit.
-constexpr int SEG_GROUP_MAX = 32;
+// the smallest group needs the least shared memory: a grid is accepted when it fits
+size_t project_smem_bytes(const GeomDev &G) { return project_smem(G, PROJECT_GROUP_SIZES[0]); }
 
-__device__ __forceinline__ int lower_count(const float *a, int n, float t) // # a[i] < t
+static const void *kernel_for(int sg, int mode, int storage)
 {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a[mid] < t) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int upper_count(const float *a, int n, float t) // # a[i] <= t
-{
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a[mid] <= t) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-// segments of a trace (at most nx + ny + 1), padded to whole groups
-static inline int seg_capacity(const GeomDev &G, int sg)
-{
-    return ((G.nx + G.ny + 2 + sg - 1) / sg) * sg;
-}
-
-static inline size_t project_smem(const GeomDev &G, int sg);
-
-static inline int segment_group(const GeomDev &G)
-{
-    return project_smem(G, SEG_GROUP_MAX) <= PROJECT_SMEM_LIMIT ? SEG_GROUP_MAX : SEG_GROUP_MAX / 2;
-}
-
-// Shared memory of one block: the two crossing lists, then (16-byte aligned) per segment
-// its end tau, its column offset and the packed record used by the walk.
-static inline int seg_offset(const GeomDev &G) { return ((G.nx + G.ny + 2 + 3) / 4) * 4; }
-
-// z-lines of one group of columns, staged in shared memory one line per column. A column
-// starts at float offset col of the z-contiguous volume; its line is copied in 16-byte
-// pieces from col rounded down to a multiple of 4 up to col + nz rounded up, i.e. at most
-// nz + 6 floats, and the column's first voxel sits at (col & 3) in its line. The copy may
-// read up to 3 floats past the last voxel of the volume: every volume buffer the
-// projector reads has at least 16 bytes of slack after it (PROJECT_VOLUME_SLACK).
-static inline int line_pitch(int nz) { return ((nz + 6 + 3) / 4) * 4; }
-
-// shared memory: per segment (end tau, column offset, (line offset, length)); then two
-// staged groups of z-lines, whose space first holds phase 1's crossing lists; then the
-// group's per-slab prefix table and two rows of running per-slab totals
-static inline size_t line_region(const GeomDev &G, int sg)
-{
-    const size_t lines = 2 * (size_t)sg * line_pitch(G.nz), lists = (size_t)seg_offset(G);
-    return lines > lists ? lines : lists;
-}
-
-static inline size_t project_smem(const GeomDev &G, int sg)
-{
-    return (sizeof(float) + sizeof(int) + sizeof(float2)) * (size_t)seg_capacity(G, sg) +
-           sizeof(float) * (line_region(G, sg) + (size_t)G.nz * (sg + 1) + 2 * (size_t)G.nz);
-}
-
-size_t project_smem_bytes(const GeomDev &G) { return project_smem(G, segment_group(G)); }
-
-// 16-byte asynchronous global -> shared copy (L2 only); both addresses 16-byte aligned
-__device__ __forceinline__ void cp_async16(float *smem_dst, const float *gsrc)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-// One block per (view, imager column, chunk of rows), volume z-contiguous (sz = 1).
-// Phase 1 (whole block): the transverse Siddon trace of the column's rays — the
-// crossings with the x planes and with the y planes are each increasing in tau, so every
-// crossing's position in the merged order is its own index plus the number of crossings
-// of the other family before it (binary search); this yields the list of (x, y) voxel
-// columns the rays visit and the tau at which each is left. For every segment the block
-// also stores its length and where its column's z-line will sit in shared memory.
-// Phase 2, per group of SG segments: the block stages the group's z-lines and builds
-// the per-slab prefix table T[k][u] over the group's columns; then each thread (two
-// imager rows) adds, for each run of whole columns a row spends in one z slab, the
-// table difference, and splits exactly each column in which the row crosses a z plane.
-template <int MODE, typename TP, int SG>
-__global__ void __launch_bounds__(PROJ_THREADS, CBCT_PROJ_MIN_BLOCKS)
-k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *__restrict__ y,
-          TP *__restrict__ out, double *__restrict__ partials, float count_thr, const Scalars *__restrict__ sc)
-{
-    extern __shared__ __align__(16) float smem[];
-    __shared__ double s_warp[PROJ_THREADS / 32];
-    const int cap = ((G.nx + G.ny + 2 + SG - 1) / SG) * SG;
-    float *sEnd = smem;                                    // tau at which segment j ends
-    int *sCol = reinterpret_cast<int *>(sEnd + cap);      // voxel-column offset of segment j
-    float2 *sSeg = reinterpret_cast<float2 *>(sCol + cap); // (line offset bits, length) of segment j
-    const int pitch = ((G.nz + 6 + 3) / 4) * 4;            // floats per staged line
-    const int quads = pitch / 4;                           // 16-byte pieces per line slot
-    float *sLine = reinterpret_cast<float *>(sSeg + cap);  // two staged groups of z-lines
-    float *sA = sLine;                                     // phase 1: x-plane crossings, in ray order
-    float *sB = sA + (G.nx + 1);                           // phase 1: y-plane crossings
-    const int lregion = max(2 * SG * pitch, ((G.nx + G.ny + 2 + 3) / 4) * 4);
-    constexpr int TPITCH = SG + 1;                         // odd: the build's threads (slabs) hit distinct banks
-    float *sTab = sLine + lregion;                         // [nz][SG + 1] per-slab prefix table
-    float *sBase = sTab + G.nz * TPITCH;                   // [2][nz] running per-slab totals
-
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int view = blockIdx.x / G.nu;
-    const int iu = blockIdx.x - view * G.nu;
-
-    // ---- transverse ray, shared by every row ----
-    const float2 cs = G.cs[view];
-    float dxr, dyr, qx, qy;
-    ray_xy(G, cs.x, cs.y, imager_u(G, iu), dxr, dyr, qx, qy);
-    const float inv_x = safe_rcp(dxr), inv_y = safe_rcp(dyr);
-    const float xa = tau_plane(G.x0, qx, inv_x), xb = tau_plane(plane_at(G.nx, G.dx, G.x0), qx, inv_x);
-    const float ya = tau_plane(G.y0, qy, inv_y), yb = tau_plane(plane_at(G.ny, G.dy, G.y0), qy, inv_y);
-    const float tau_in = fmaxf(fmaxf(fminf(xa, xb), fminf(ya, yb)), -G.tc);
-    const float tau_out = fminf(fminf(fmaxf(xa, xb), fmaxf(ya, yb)), 1.0f - G.tc);
-    const bool hit = tau_in < tau_out;
-    const int sxs = dxr > 0.0f ? 1 : -1, sys = dyr > 0.0f ? 1 : -1;
-
-    // ---- phase 1: crossings of each plane family, then their merged order ----
-    int a_le = 0, a_in = 0, b_le = 0, b_in = 0;
-    for (int a0 = 0; a0 <= G.nx; a0 += nthr) {
-        const int a = a0 + tid;
-        bool le = false, in = false;
-        if (a <= G.nx && hit && dxr != 0.0f) {
-            const float t = tau_plane(plane_at(dxr > 0.0f ? a : G.nx - a, G.dx, G.x0), qx, inv_x);
-            sA[a] = t;
-            le = t <= tau_in;
-            in = t > tau_in && t < tau_out;
-        }
-        a_le += __syncthreads_count(le);
-        a_in += __syncthreads_count(in);
-    }
-    for (int b0 = 0; b0 <= G.ny; b0 += nthr) {
-        const int b = b0 + tid;
-        bool le = false, in = false;
-        if (b <= G.ny && hit && dyr != 0.0f) {
-            const float t = tau_plane(plane_at(dyr > 0.0f ? b : G.ny - b, G.dy, G.y0), qy, inv_y);
-            sB[b] = t;
-            le = t <= tau_in;
-            in = t > tau_in && t < tau_out;
-        }
-        b_le += __syncthreads_count(le);
-        b_in += __syncthreads_count(in);
-    }
-    const float *LA = sA + a_le, *LB = sB + b_le;
-    const int nA = a_in, nB = b_in, nseg = nA + nB + 1;
-    // the column entered first contains the midpoint of the first segment
-    float e0 = tau_out;
-    if (nA) e0 = fminf(e0, LA[0]);
-    if (nB) e0 = fminf(e0, LB[0]);
-    const float tm = 0.5f * (tau_in + e0);
-    const int ix_e = min(max((int)floorf((fmaf(tm, dxr, qx) - G.x0) / G.dx), 0), G.nx - 1);
-    const int iy_e = min(max((int)floorf((fmaf(tm, dyr, qy) - G.y0) / G.dy), 0), G.ny - 1);
-    for (int i = tid; i < nA; i += nthr) {
-        const float t = LA[i];
-        const int nb = lower_count(LB, nB, t), r = i + nb;
-        const int cx = min(max(ix_e + sxs * (i + 1), 0), G.nx - 1), cy = min(max(iy_e + sys * nb, 0), G.ny - 1);
-        sEnd[r] = t;
-        sCol[r + 1] = cx * sx + cy * sy;
-    }
-    for (int j = tid; j < nB; j += nthr) {
-        const float t = LB[j];
-        const int na = upper_count(LA, nA, t), r = j + na;
-        const int cx = min(max(ix_e + sxs * na, 0), G.nx - 1), cy = min(max(iy_e + sys * (j + 1), 0), G.ny - 1);
-        sEnd[r] = t;
-        sCol[r + 1] = cx * sx + cy * sy;
-    }
-    const int col0 = ix_e * sx + iy_e * sy;
-    if (tid == 0) {
-        sCol[0] = col0;
-        sEnd[nseg - 1] = tau_out;
-    }
-    for (int q = nseg + tid; q < cap; q += nthr) { // zero-length padding up to whole groups
-        sEnd[q] = tau_out;
-        sCol[q] = col0;
-    }
-    __syncthreads();
-    for (int q = tid; q < cap; q += nthr) {
-        const float st = q ? sEnd[q - 1] : tau_in;
-        // where the column's first voxel lands in its staged line
-        const int loff = (q % SG) * pitch + (sCol[q] & 3);
-        sSeg[q] = make_float2(__int_as_float(loff), sEnd[q] - st);
-    }
-    __syncthreads();
-
-    // ---- phase 2: per-row z state (two rows per thread: iv[0] and iv[1] = iv[0] + nthr) ----
-    constexpr int R = 2;
-    int iv[R], skz[R], kz[R];
-    float inv_v[R], tzn[R], L[R], acc[R];
-    bool ok[R], active[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        iv[r] = blockIdx.y * (R * nthr) + r * nthr + tid;
-        ok[r] = iv[r] < G.nv;
-        const float v = imager_v(G, iv[r]);
-        inv_v[r] = v != 0.0f ? __frcp_rn(v) : 1e30f;
-        skz[r] = v >= 0.0f ? 1 : -1;
-        kz[r] = (int)floorf((v * (G.tc + tau_in) - G.z0) / G.dz);
-        active[r] = hit && ok[r] && kz[r] >= 0 && kz[r] < G.nz;
-        tzn[r] = active[r] ? tau_zplane(plane_at(kz[r] + (skz[r] > 0), G.dz, G.z0), inv_v[r], G.tc) : P_INF;
-        if (active[r] && tzn[r] <= tau_in) { // the entry point already lies past that plane
-            kz[r] += skz[r];
-            active[r] = (unsigned)kz[r] < (unsigned)G.nz;
-            tzn[r] = active[r] ? tau_zplane(plane_at(kz[r] + (skz[r] > 0), G.dz, G.z0), inv_v[r], G.tc) : P_INF;
-        }
-        L[r] = ray_length(dxr, dyr, v);
-        acc[r] = 0.0f;
-    }
-
-    int cnt = 0;
-    if (hit && MODE == PM_COUNT) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const float thr_tau = count_thr / L[r];
-            float s0 = tau_in;
-            for (int j = 0; j < nseg; ++j) {
-                const float e = sEnd[j];
-                float sl = s0;
-                while (tzn[r] < e) {
-                    cnt += (tzn[r] - sl) > thr_tau;
-                    sl = tzn[r];
-                    kz[r] += skz[r];
-                    active[r] = (unsigned)kz[r] < (unsigned)G.nz;
-                    tzn[r] = active[r] ? tau_zplane(plane_at(kz[r] + (skz[r] > 0), G.dz, G.z0), inv_v[r], G.tc) : P_INF;
-                }
-                if (active[r]) cnt += (e - sl) > thr_tau;
-                s0 = e;
-            }
-        }
-    } else if (hit) {
-        // Per group of SG segments: stage the z-lines of its columns (16-byte cp.async,
-        // one group ahead), build once for the block the per-slab prefix table over the
-        // group's columns,
-        //     T[k][u] = sum_{u' < u} f(column u', slab k) * length(u'),   u = 0..SG,
-        // and let every row add T[k][u1] - T[k][u0] for each run of whole columns it
-        // spends in slab k. Only the columns in which a row crosses a z plane are split,
-        // exactly, at the crossing. A block has far more rows than slabs, so the table
-        // does the per-column work once per slab instead of once per row.
-        const int nchunk = (nseg + SG - 1) / SG;
-        // 16-byte pieces of a group's lines: slot c = (line u, piece i), c = u * quads + i;
-        // thread tid takes c = tid, tid + nthr, ... (the same slots for every group)
-        const int u_0 = tid / quads, i_0 = tid - u_0 * quads;
-        const int du = nthr / quads, di = nthr - du * quads;
-        auto fill = [&](int chunk, int buf) {
-            float *dst = sLine + buf * SG * pitch;
-            const int *col = sCol + chunk * SG;
-            for (int u = u_0, i = i_0; u < SG;) {
-                const int c0 = col[u];
-                const int first = c0 & ~3, last = (c0 + G.nz + 3) & ~3; // 16-byte rounded line
-                if (first + 4 * i < last) cp_async16(dst + u * pitch + 4 * i, f + first + 4 * i);
-                u += du;
-                i += di;
-                if (i >= quads) {
-                    i -= quads;
-                    ++u;
-                }
-            }
-            cp_async_commit();
-        };
-        const bool split = nthr >= 2 * G.nz;
-        const float inv_dx = 1.0f / G.dx, inv_dy = 1.0f / G.dy;
-        // T[k][u]: the table entry, plus the first half's total for a second-half entry
-        auto tab = [&](int k, int u) {
-            const float *trow = sTab + k * TPITCH;
-            return split && u > SG / 2 ? trow[u] + trow[SG / 2] : trow[u];
-        };
-        float E[R] = {0.0f, 0.0f}; // running total where each row's current run starts
-        for (int k = tid; k < G.nz; k += nthr) sBase[k] = 0.0f; // published by the first barrier
-        fill(0, 0);
-        float g0 = tau_in;
-        for (int ch = 0; ch < nchunk; ++ch) {
-            const int j = ch * SG;
-            if (ch + 1 < nchunk) {
-                fill(ch + 1, (ch + 1) & 1);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
-            __syncthreads();
-            const float *lines = sLine + (ch & 1) * SG * pitch;
-            // The group's prefix table. With threads to spare each slab's running sum is
-            // split into two chains of SG / 2 columns computed side by side; the second
-            // half's entries then hold sums from column SG / 2 on, and tab() adds the
-            // first half's total.
-            if (split) {
-                for (int task = tid; task < 2 * G.nz; task += nthr) {
-                    const int k = task >> 1, h = (task & 1) * (SG / 2);
-                    float *trow = sTab + k * TPITCH + h;
-                    float sum = 0.0f;
-                    if (!h) trow[0] = 0.0f;
-#pragma unroll 8
-                    for (int u = 0; u < SG / 2; ++u) {
-                        const float2 seg = sSeg[j + h + u]; // (line offset, length)
-                        sum = fmaf(lines[__float_as_int(seg.x) + k], seg.y, sum);
-                        trow[u + 1] = sum;
-                    }
-                }
-            } else {
-                for (int k = tid; k < G.nz; k += nthr) {
-                    float *trow = sTab + k * TPITCH;
-                    float sum = 0.0f;
-                    trow[0] = 0.0f;
-#pragma unroll 8
-                    for (int u = 0; u < SG; ++u) {
-                        const float2 seg = sSeg[j + u];
-                        sum = fmaf(lines[__float_as_int(seg.x) + k], seg.y, sum);
-                        trow[u + 1] = sum;
-                    }
-                }
-            }
-            __syncthreads();
-            const float gend = sEnd[j + SG - 1];
-            // running per-slab totals: C[k][j + u] = base[k] + T[k][u] is the sum over all
-            // columns of the trace before column j + u; one thread per slab carries it on
-            const float *bcur = sBase + (ch & 1) * G.nz;
-            float *bnext = sBase + ((ch + 1) & 1) * G.nz;
-            for (int k = tid; k < G.nz; k += nthr) bnext[k] = bcur[k] + tab(k, SG);
-            // A row does nothing in a group it crosses no z plane in. At a crossing it adds
-            // its run in the slab it leaves (a difference of running totals, plus the part
-            // of the crossing column before the plane) and books the rest of that column to
-            // the slab it enters; E remembers the running total where that slab's run of
-            // whole columns starts.
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float a = acc[r];
-                int cpend = -1; // column of this row's previous crossing in this group
-                while (tzn[r] < gend) { // a z crossing inside this group (the row is active)
-                    const float t = tzn[r];
-                    // The segment holding the crossing: the x and y planes the ray has passed
-                    // at t, from its transverse position (no search). At a near tie this may
-                    // name the neighbouring segment, which only moves a rounding-sized piece
-                    // of length between two adjacent columns; it is kept monotone.
-                    int na = (int)floorf((fmaf(t, dxr, qx) - G.x0) * inv_dx) - ix_e;
-                    int nb = (int)floorf((fmaf(t, dyr, qy) - G.y0) * inv_dy) - iy_e;
-                    na = min(max(sxs > 0 ? na : -na, 0), nA);
-                    nb = min(max(sys > 0 ? nb : -nb, 0), nB);
-                    const int c = min(max(na + nb - j, max(cpend, 0)), SG - 1);
-                    const int lo = __float_as_int(sSeg[j + c].x);
-                    const float en = sEnd[j + c];
-                    const float fcur = lines[lo + kz[r]];
-                    if (c == cpend) // entered this slab in this same column: trim the booked rest
-                        a = fmaf(-fcur, en - t, a);
-                    else
-                        a += (bcur[kz[r]] + tab(kz[r], c)) - E[r] +
-                             fcur * fmaxf(t - (c ? sEnd[j + c - 1] : g0), 0.0f);
-                    cpend = c;
-                    kz[r] += skz[r];
-                    active[r] = (unsigned)kz[r] < (unsigned)G.nz;
-                    if (active[r]) {
-                        a = fmaf(lines[lo + kz[r]], en - t, a);
-                        E[r] = bcur[kz[r]] + tab(kz[r], c + 1);
-                    }
-                    tzn[r] = active[r] ? tau_zplane(plane_at(kz[r] + (skz[r] > 0), G.dz, G.z0), inv_v[r], G.tc) : P_INF;
-                }
-                acc[r] = a;
-            }
-            g0 = gend;
-            __syncthreads();
-        }
-        // the run each still-active row ends in: up to the end of the trace
-        const float *bend = sBase + (nchunk & 1) * G.nz;
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-            if (active[r]) acc[r] += bend[kz[r]] - E[r];
-    }
-
-    // ---- epilogue ----
-    double red = 0.0;
-    const float kappa = (MODE == PM_Q_SCALED) ? (float)sc->kappa : 1.0f;
-    constexpr bool PRESCALE = sizeof(TP) == 4;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        if (!ok[r]) continue;
-        const size_t idx = ((size_t)view * G.nv + iv[r]) * G.nu + iu;
-        const float q = acc[r] * L[r];
-        // FP32 storage keeps |D - S| folded into r and q (the adjoint then needs no
-        // per-sample rescale); 16-bit storage keeps the bare values
-        const float s = PRESCALE ? L[r] : 1.0f;
-        if (MODE == PM_PLAIN) {
-            store_from_float(out + idx, q);
-        } else if (MODE == PM_Q_SCALED) {
-            store_from_float(out + idx, q * s * kappa);
-            red += (double)q * (double)q;
-        } else if (MODE == PM_RESID) {
-            const float rr = __ldg(y + idx) - q;
-            store_from_float(out + idx, rr * s);
-            red += (double)rr * (double)rr;
-        }
-    }
-    if (MODE == PM_COUNT) red = (double)cnt;
-    if (MODE != PM_PLAIN) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) red += __shfl_down_sync(0xffffffffu, red, o);
-        if ((tid & 31) == 0) s_warp[tid >> 5] = red;
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < (nthr + 31) / 32; ++w) t += s_warp[w];
-            partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
-        }
+    switch (sg) {
+    case 16: return project_kernel<16>(mode, storage);
+    case 24: return project_kernel<24>(mode, storage);
+    case 32: return project_kernel<32>(mode, storage);
+    case 40: return project_kernel<40>(mode, storage);
+    case 48: return project_kernel<48>(mode, storage);
+    case 56: return project_kernel<56>(mode, storage);
+    case 64: return project_kernel<64>(mode, storage);
+    case 80: return project_kernel<80>(mode, storage);
+    case 96: return project_kernel<96>(mode, storage);
+    default: return nullptr;
     }
 }
 
-// per-device record of the shared-memory opt-in, one per kernel instantiation
-// per-device record of the shared-memory opt-in, one per kernel instantiation
-template <int MODE, typename TP, int SG> static std::atomic<unsigned long long> g_project_optin{0};
-
-template <int MODE, typename TP> static cbct_status project_optin()
+static int group_index(int sg)
 {
-    cudaError_t e = smem_optin_once(k_project<MODE, TP, SEG_GROUP_MAX>, (int)PROJECT_SMEM_LIMIT, g_project_optin<MODE, TP, SEG_GROUP_MAX>);
-    if (e == cudaSuccess)
-        e = smem_optin_once(k_project<MODE, TP, SEG_GROUP_MAX / 2>, (int)PROJECT_SMEM_LIMIT, g_project_optin<MODE, TP, SEG_GROUP_MAX / 2>);
-    return e == cudaSuccess ? CBCT_OK : check_cuda(e, "project attribute");
+    for (int i = 0; i < PROJECT_N_GROUP_SIZES; ++i)
+        if (PROJECT_GROUP_SIZES[i] == sg) return i;
+    return -1;
 }
 
-template <int MODE, typename TP>
-static cbct_status launch_project_t(const GeomDev &G, const float *f, int isx, int isy, const float *y, void *out,
-                                   double *partials, float count_thr, const Scalars *sc, dim3 grid, int threads,
-                                   int sg, size_t smem, cudaStream_t st)
+// per-device record of the shared-memory opt-in, one per (group size, mode, storage)
+static std::atomic<unsigned long long> g_optin[PROJECT_N_GROUP_SIZES][4][3];
+
+static cbct_status optin(int sg, int mode, int storage, const void **fn)
 {
-    {
-        cbct_status a = project_optin<MODE, TP>();
-        if (a != CBCT_OK) return a;
-    }
-    if (sg == SEG_GROUP_MAX)
-        k_project<MODE, TP, SEG_GROUP_MAX><<<grid, threads, smem, st>>>(G, f, isx, isy, y, static_cast<TP *>(out),
-                                                                       partials, count_thr, sc);
-    else
-        k_project<MODE, TP, SEG_GROUP_MAX / 2><<<grid, threads, smem, st>>>(G, f, isx, isy, y, static_cast<TP *>(out),
-                                                                           partials, count_thr, sc);
+    *fn = kernel_for(sg, mode, storage);
+    if (!*fn) return set_error(CBCT_ERR_UNSUPPORTED, "project: no kernel for group %d, mode %d", sg, mode);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return check_cuda(e, "project device");
+    std::atomic<unsigned long long> &done = g_optin[group_index(sg)][mode][storage == ST_BF16 ? 1 : storage == ST_F16 ? 2 : 0];
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load() & bit) return CBCT_OK;
+    e = cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PROJECT_SMEM_LIMIT);
+    if (e != cudaSuccess) return check_cuda(e, "project attribute");
+    done.fetch_or(bit);
     return CBCT_OK;
 }
 
+static std::atomic<int> g_forced_group{0}; // 0: automatic
+
+// The group size of a launch: the largest size that keeps as many blocks of this kernel
+// resident per SM as any size does (the occupancy query counts registers, threads and
+// shared memory), among the sizes whose shared memory fits. Cached per device, mode,
+// storage, block size and the grid extents the shared memory depends on.
+static cbct_status choose_group(const GeomDev &G, int threads, int mode, int storage, int *sg_out)
+{
+    const int forced = g_forced_group.load();
+    if (mode == PM_COUNT) {
+        *sg_out = PROJECT_GROUP_SIZES[0];
+        return CBCT_OK;
+    }
+    if (forced && project_smem(G, forced) <= PROJECT_SMEM_LIMIT) {
+        *sg_out = forced;
+        return CBCT_OK;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return check_cuda(e, "project device");
+    using Key = std::tuple<int, int, int, int, int, int>;
+    static std::mutex mu;
+    static std::map<Key, int> cache;
+    const Key key{dev, mode, storage, threads, G.nz, G.nx + G.ny};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            *sg_out = it->second;
+            return CBCT_OK;
+        }
+    }
+    int best = PROJECT_GROUP_SIZES[0], best_nb = -1;
+    for (int i = 0; i < PROJECT_N_GROUP_SIZES; ++i) {
+        const int sg = PROJECT_GROUP_SIZES[i];
+        const size_t smem = project_smem(G, sg);
+        if (smem > PROJECT_SMEM_LIMIT) break; // grows with sg
+        const void *fn = nullptr;
+        cbct_status r = optin(sg, mode, storage, &fn);
+        if (r != CBCT_OK) return r;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem);
+        if (e != cudaSuccess) return check_cuda(e, "project occupancy");
+        if (nb >= best_nb) { // ties go to the larger group
+            best_nb = nb;
+            best = sg;
+        }
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = best;
+    *sg_out = best;
+    return CBCT_OK;
+}
+
+cbct_status project_set_group(int sg)
+{
+    if (sg != 0 && group_index(sg) < 0)
+        return set_error(CBCT_ERR_INVALID_ARG, "set_project_group: %d is not one of the compiled group sizes", sg);
+    g_forced_group.store(sg);
+    return CBCT_OK;
+}
+
+cbct_status project_group_of(const GeomDev &G, int *sg) { return choose_group(G, proj_threads(G), PM_PLAIN, ST_F32, sg); }
+
 cbct_status project_prepare()
 {
-    cbct_status r = CBCT_OK;
-    if (r == CBCT_OK) r = project_optin<PM_PLAIN, float>();
-    if (r == CBCT_OK) r = project_optin<PM_PLAIN, __nv_bfloat16>();
-    if (r == CBCT_OK) r = project_optin<PM_PLAIN, __half>();
-    if (r == CBCT_OK) r = project_optin<PM_COUNT, float>();
-    if (r == CBCT_OK) r = project_optin<PM_Q_SCALED, float>();
-    if (r == CBCT_OK) r = project_optin<PM_Q_SCALED, __nv_bfloat16>();
-    if (r == CBCT_OK) r = project_optin<PM_Q_SCALED, __half>();
-    if (r == CBCT_OK) r = project_optin<PM_RESID, float>();
-    if (r == CBCT_OK) r = project_optin<PM_RESID, __nv_bfloat16>();
-    if (r == CBCT_OK) r = project_optin<PM_RESID, __half>();
-    return r;
+    for (int i = 0; i < PROJECT_N_GROUP_SIZES; ++i)
+        for (int mode = PM_PLAIN; mode <= PM_COUNT; ++mode)
+            for (int storage = ST_F32; storage <= ST_F16; ++storage) {
+                if (mode == PM_COUNT && (i > 0 || storage != ST_F32)) continue;
+                const void *fn = nullptr;
+                cbct_status r = optin(PROJECT_GROUP_SIZES[i], mode, storage, &fn);
+                if (r != CBCT_OK) return r;
+            }
+    return CBCT_OK;
 }
 
 cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long long sy,
@@ -505,42 +144,26 @@ cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long 
 {
     const int threads = proj_threads(G); // 2 rows each
     dim3 grid((unsigned)(G.nviews * G.nu), (unsigned)((G.nv + 2 * threads - 1) / (2 * threads)));
-    const int sg = segment_group(G);
-    const size_t smem = project_smem(G, sg);
-    if (smem > PROJECT_SMEM_LIMIT)
+    if (project_smem_bytes(G) > PROJECT_SMEM_LIMIT)
         return set_error(CBCT_ERR_UNSUPPORTED, "project: grid too large for the projector's shared memory (nx + ny and nz)");
     if (sz != 1) return set_error(CBCT_ERR_INVALID_ARG, "project: the volume must be z-contiguous");
-    const int isx = (int)sx, isy = (int)sy;
-    cbct_status r = CBCT_OK;
+    if (mode == PM_COUNT) storage = ST_F32;
+    int sg = 0;
+    cbct_status r = choose_group(G, threads, mode, storage, &sg);
+    if (r != CBCT_OK) return r;
+    const void *fn = nullptr;
+    r = optin(sg, mode, storage, &fn);
+    if (r != CBCT_OK) return r;
+    const size_t smem = project_smem(G, sg);
+    GeomDev g = G;
+    int isx = (int)sx, isy = (int)sy;
+    void *args[] = {&g, &f, &isx, &isy, &y, &out, &partials, &count_thr, &sc};
     ProfToken tok = prof_start(CBCT_KERNEL_PROJECT, st);
-    if (mode == PM_PLAIN) {
-        if (storage == ST_BF16)
-            r = launch_project_t<PM_PLAIN, __nv_bfloat16>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
-        else if (storage == ST_F16)
-            r = launch_project_t<PM_PLAIN, __half>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
-        else
-            r = launch_project_t<PM_PLAIN, float>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
-    } else if (mode == PM_COUNT) {
-        r = launch_project_t<PM_COUNT, float>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
-    } else if (mode == PM_Q_SCALED) {
-        if (storage == ST_BF16)
-            r = launch_project_t<PM_Q_SCALED, __nv_bfloat16>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
-        else if (storage == ST_F16)
-            r = launch_project_t<PM_Q_SCALED, __half>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
-        else
-            r = launch_project_t<PM_Q_SCALED, float>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
-    } else {
-        if (storage == ST_BF16)
-            r = launch_project_t<PM_RESID, __nv_bfloat16>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
-        else if (storage == ST_F16)
-            r = launch_project_t<PM_RESID, __half>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
-        else
-            r = launch_project_t<PM_RESID, float>(G, f, isx, isy, y, out, partials, count_thr, sc, grid, threads, sg, smem, st);
-    }
+    cudaError_t e = cudaLaunchKernel(fn, grid, dim3((unsigned)threads), args, smem, st);
     prof_stop(tok, st);
     note_launch();
-    if (r != CBCT_OK) return r;
-    return check_cuda(cudaGetLastError(), "project launch");
+    if (e != cudaSuccess) cudaGetLastError(); // the error is returned, not left pending
+    return check_cuda(e, "project launch");
 }
 
 } // namespace cbct

@@ -63,6 +63,80 @@ def test_project_parity(cb, name):
     assert rel(p, ref) <= 1e-4, rel(p, ref)
 
 
+# traces of about 200 columns: several groups of every size, with a ragged last group
+GROUP_GEOMS = {
+    "odd": GEOMS["odd"],
+    "cone": GEOMS["cone"],
+    "long": synth.Geometry(nx=101, ny=90, nz=9, dx=1.0, dy=1.1, dz=2.0, nu=60, nv=26, du=1.9, dv=1.6,
+                           u_off=0.7, v_off=-0.4, n_views=3, angles=(0.15, 1.9, 3.7)),
+}
+
+
+@pytest.fixture
+def forced_group(cb):
+    yield cb.set_project_group
+    cb.set_project_group(0)
+
+
+@pytest.mark.parametrize("sg", [16, 24, 32, 40, 48, 56, 64, 80, 96])
+def test_project_parity_every_group_size(cb, forced_group, sg):
+    """Every compiled column-group size of the projector against the oracle, and against
+    the automatic choice to FP32 rounding (the groups only re-associate the sums)."""
+    assert sg in cb.PROJECT_GROUP_SIZES
+    for name, geom in GROUP_GEOMS.items():
+        f = synth.random_volume(geom, 103)
+        with cb.Geometry(geom) as g:
+            forced_group(0)
+            auto = cb.project(g, dev(f)).cpu().numpy()
+            forced_group(sg)
+            p = cb.project(g, dev(f)).cpu().numpy()
+        ref = oracle.project(geom, f)
+        assert rel(p, ref) <= 1e-4, (name, rel(p, ref))
+        assert rel(p, auto) <= 2e-6, (name, rel(p, auto))
+
+
+@pytest.mark.parametrize("sg", [16, 56, 96])
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_reconstruct_parity_forced_group_sizes(cb, forced_group, sg, storage):
+    """The CGLS projector modes (scaled direction, residual; FP32 and BF16 storage) under
+    forced group sizes: a short reconstruction against the oracle."""
+    geom = GROUP_GEOMS["long"]
+    f_true = synth.voxelize(geom, synth.random_ellipsoids(geom, 104))
+    y = synth.noisy_line_integrals(oracle.project(geom, f_true), 1e5, 105)
+    forced_group(sg)
+    with cb.Geometry(geom) as g:
+        x = cb.reconstruct(g, dev(y), 5e-4, 1, [6], storage=storage).cpu().numpy()
+    ref = oracle.reconstruct(geom, y, 5e-4, 1, [6], storage=0 if storage == "f32" else storage)
+    assert rel(x, ref) <= 1e-3, rel(x, ref)
+
+
+def test_project_group_choice(cb, forced_group):
+    """The automatic choice is a compiled size; forcing names a compiled size or 0; a forced
+    size whose shared memory does not fit leaves that grid on the automatic choice."""
+    geom = synth.config_paper(40)
+    with cb.Geometry(geom) as g:
+        auto = [cb.project_group(g, lv) for lv in range(3)]
+        assert all(a in cb.PROJECT_GROUP_SIZES for a in auto)
+        forced_group(24)
+        assert cb.project_group(g, 0) == 24
+        with pytest.raises(cb.CbctError) as e:
+            forced_group(33)
+        assert e.value.status == 1
+        assert cb.project_group(g, 0) == 24  # an invalid call changes nothing
+        forced_group(0)
+        assert [cb.project_group(g, lv) for lv in range(3)] == auto
+    big = LARGEST_NZ
+    with cb.Geometry(big) as g:
+        forced_group(0)
+        a = cb.project_group(g, 0)
+        forced_group(96)  # 96 columns of 950-voxel lines exceed the shared memory
+        assert cb.project_group(g, 0) == a
+
+
+LARGEST_NZ = synth.Geometry(nx=256, ny=256, nz=950, dx=1.0, dy=1.0, dz=0.2, nu=64, nv=40, du=1.5, dv=1.5,
+                            n_views=2, angles=(0.1, 1.7))
+
+
 @pytest.mark.parametrize("name", list(GEOMS))
 def test_backproject_parity(cb, name):
     geom = GEOMS[name]
