@@ -382,9 +382,10 @@ cbct_status cbct_server_destroy(cbct_server *srv);
 /*
  * Column groups of the projector (tuning and testing; not part of the paper's method).
  * Along each ray's transverse trace (Section 2.2.1's Siddon walk) the projector stages the
- * voxel columns in groups of 16, 24, 32, 40, 48, 56, 64, 80 or 96 and, by default, gives
- * each launch the largest group that keeps the most blocks resident per SM. Results of
- * different group sizes agree to FP32 rounding (the sums are associated differently).
+ * voxel columns in groups of 16, 24, 32, 40, 48, 56, 64, 80 or 96 and, by default, picks
+ * the size per launch from an estimate of its per-group cost and of the blocks it keeps
+ * resident per SM. Results of different group sizes agree to FP32 rounding (the sums are
+ * associated differently).
  *
  * cbct_set_project_group: process-wide; 0 restores the automatic choice, one of the sizes
  * above forces it for every launch whose shared memory it fits (larger grids keep the

