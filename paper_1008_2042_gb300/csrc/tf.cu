@@ -280,17 +280,28 @@ namespace cbct {
 // The coefficients never leave the SM: HBM traffic is one read of x (plus halo re-reads
 // that hit L2) and the writes of f_new (and v, with one read of f_old).
 // ------------------------------------------------------------------------------------
-constexpr int FX_A = TA + 4, FX_B = TB + 4;  // x tile with a two-voxel halo
-constexpr int FA_A = TA + 2, FA_B = TB + 2;  // coefficient tile with a one-voxel halo
-constexpr int FX_PLANE = FX_A * FX_B;
-constexpr int FA_PLANE = FA_A * FA_B;
-constexpr int FU_PLANE = FA_B * TA;
-constexpr size_t TF_FUSED_SMEM = sizeof(float) * (3 * FX_PLANE + 27 * FA_PLANE + 9 * FU_PLANE);
+// The tile is TAF x TB (TAF = 24, 32 or 36 along axis 0, chosen per launch so that the
+// tiles cover axis 0 with the fewest idle columns: 70 = 3 x 24 - 2, 35 = 36 - 1).
+template <int TAF> struct FusedTile {
+    static constexpr int NT = TAF * TB;                      // threads
+    static constexpr int FX_A = TAF + 4, FX_B = TB + 4;      // x tile with a two-voxel halo
+    static constexpr int FA_A = TAF + 2, FA_B = TB + 2;      // coefficient tile with a one-voxel halo
+    static constexpr int FX_PLANE = FX_A * FX_B;
+    static constexpr int FA_PLANE = FA_A * FA_B;
+    static constexpr int FU_PLANE = FA_B * TAF;
+    static constexpr size_t SMEM = sizeof(float) * (3 * FX_PLANE + 27 * FA_PLANE + 9 * FU_PLANE);
+    static_assert(2 * NT >= FX_PLANE, "two x-tile positions per thread");
+};
 
-__global__ void __launch_bounds__(TF_THREADS)
+template <int TAF>
+__global__ void __launch_bounds__(TAF * TB)
 k_tf_shrink_fused(int n0, int n1, int n2, int chunk, const float *__restrict__ x, float mu, int positivity,
                   float *__restrict__ fnew, const float *__restrict__ fold, float coef, float *__restrict__ vout)
 {
+    using T = FusedTile<TAF>;
+    constexpr int TA = TAF, TF_THREADS = T::NT;
+    constexpr int FX_A = T::FX_A, FX_PLANE = T::FX_PLANE, FA_A = T::FA_A, FA_PLANE = T::FA_PLANE,
+                  FU_PLANE = T::FU_PLANE;
     extern __shared__ float sm[];
     float *sx = sm;                         // [3][FX_B][FX_A] ring of x planes
     float *sa = sx + 3 * FX_PLANE;          // [27][FA_B][FA_A] shrunk coefficients of plane c'
@@ -399,11 +410,11 @@ k_tf_shrink_fused(int n0, int n1, int n2, int chunk, const float *__restrict__ x
     }
 }
 
-static std::atomic<unsigned long long> g_fused_optin{0};
+template <int TAF> static std::atomic<unsigned long long> g_fused_optin{0};
 
-static cbct_status fused_optin()
+template <int TAF> static cbct_status fused_optin()
 {
-    cudaError_t e = smem_optin_once(k_tf_shrink_fused, (int)TF_FUSED_SMEM, g_fused_optin);
+    cudaError_t e = smem_optin_once(k_tf_shrink_fused<TAF>, (int)FusedTile<TAF>::SMEM, g_fused_optin<TAF>);
     return e == cudaSuccess ? CBCT_OK : check_cuda(e, "tf_shrink_fused attribute");
 }
 
@@ -412,23 +423,68 @@ cbct_status tf_prepare()
     cbct_status r = synth_optin<float>();
     if (r == CBCT_OK) r = synth_optin<__nv_bfloat16>();
     if (r == CBCT_OK) r = synth_optin<__half>();
-    if (r == CBCT_OK) r = fused_optin();
+    if (r == CBCT_OK) r = fused_optin<24>();
+    if (r == CBCT_OK) r = fused_optin<32>();
+    if (r == CBCT_OK) r = fused_optin<36>();
     return r;
+}
+
+// Planes per block along axis 2 for the fused step: the split whose blocks fill whole
+// waves of the resident slots best, counting the two extra planes each block recomputes
+// at its start (a block's cost grows with chunk + 2).
+static int fused_chunk(long long tiles, int n2, int slots)
+{
+    int best = n2;
+    double best_eff = -1.0;
+    for (int nch = 1; nch <= n2; ++nch) {
+        const int chunk = (n2 + nch - 1) / nch;
+        if (nch > 1 && chunk == (n2 + nch - 2) / (nch - 1)) continue; // same split as nch - 1
+        const long long nb = tiles * ((n2 + chunk - 1) / chunk);
+        const long long waves = (nb + slots - 1) / slots;
+        const double eff = (double)n2 / ((double)((n2 + chunk - 1) / chunk) * (chunk + 2)) * (double)nb /
+                           ((double)waves * slots);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = chunk;
+        }
+    }
+    return best;
+}
+
+template <int TAF>
+static cbct_status launch_fused_t(int n0, int n1, int n2, const float *x, float mu, int positivity, float *fnew,
+                                  const float *fold, float coef, float *vout, cudaStream_t st)
+{
+    cbct_status a = fused_optin<TAF>();
+    if (a != CBCT_OK) return a;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tf_shrink_fused<TAF>, TAF * TB,
+                                                                  FusedTile<TAF>::SMEM);
+    if (e != cudaSuccess) return check_cuda(e, "tf_shrink_fused occupancy");
+    const long long tiles = (long long)((n0 + TAF - 1) / TAF) * ((n1 + TB - 1) / TB);
+    const int chunk = fused_chunk(tiles, n2, (per_sm > 0 ? per_sm : 1) * device_sm_count());
+    dim3 grid((n0 + TAF - 1) / TAF, (n1 + TB - 1) / TB, (n2 + chunk - 1) / chunk);
+    CBCT_TIMED(CBCT_KERNEL_TF_SYNTH, st,
+               k_tf_shrink_fused<TAF><<<grid, dim3(TAF, TB), FusedTile<TAF>::SMEM, st>>>(
+                   n0, n1, n2, chunk, x, mu, positivity, fnew, fold, coef, vout));
+    return check_cuda(cudaGetLastError(), "tf_shrink_fused launch");
 }
 
 cbct_status launch_tf_shrink_fused(int n0, int n1, int n2, const float *x, float mu, int positivity, float *fnew,
                                    const float *fold, float coef, float *vout, cudaStream_t st)
 {
-    {
-        cbct_status a = fused_optin();
-        if (a != CBCT_OK) return a;
+    // the tile width covering axis 0 with the fewest columns (ties: the narrower tile)
+    int taf = 24, cover = ((n0 + 23) / 24) * 24;
+    for (int w : {32, 36}) {
+        const int c = ((n0 + w - 1) / w) * w;
+        if (c < cover) {
+            cover = c;
+            taf = w;
+        }
     }
-    const int chunk = tf_chunk(n0, n1, n2);
-    dim3 grid((n0 + TA - 1) / TA, (n1 + TB - 1) / TB, (n2 + chunk - 1) / chunk);
-    CBCT_TIMED(CBCT_KERNEL_TF_SYNTH, st,
-               k_tf_shrink_fused<<<grid, dim3(TA, TB), TF_FUSED_SMEM, st>>>(n0, n1, n2, chunk, x, mu, positivity,
-                                                                            fnew, fold, coef, vout));
-    return check_cuda(cudaGetLastError(), "tf_shrink_fused launch");
+    if (taf == 32) return launch_fused_t<32>(n0, n1, n2, x, mu, positivity, fnew, fold, coef, vout, st);
+    if (taf == 36) return launch_fused_t<36>(n0, n1, n2, x, mu, positivity, fnew, fold, coef, vout, st);
+    return launch_fused_t<24>(n0, n1, n2, x, mu, positivity, fnew, fold, coef, vout, st);
 }
 
 } // namespace cbct
