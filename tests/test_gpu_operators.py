@@ -213,7 +213,13 @@ def test_tf_synthesize_shrink_parity(cb, shape, positive):
     assert rel(out, ref) <= 1e-5, rel(out, ref)
 
 
-@pytest.mark.parametrize("shape", TF_SHAPES)
+# the fused step's tile width along the contiguous (last) axis is chosen per launch from
+# 24, 32 and 36: these cover each width (70 = 3 x 24 - 2, 35 = 36 - 1, 64 = 2 x 32) and a
+# long marching axis split into several blocks
+FUSED_SHAPES = TF_SHAPES + [(6, 9, 70), (5, 4, 35), (300, 3, 5)]
+
+
+@pytest.mark.parametrize("shape", FUSED_SHAPES)
 @pytest.mark.parametrize("positive", [False, True])
 def test_tf_shrink_fused_parity(cb, shape, positive):
     """The fused regularisation step H(W^T T_mu W f) against the oracle's three steps."""
