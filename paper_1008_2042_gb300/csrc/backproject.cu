@@ -22,11 +22,25 @@ namespace cbct {
 
 constexpr int BP_TX = 32, BP_TY = 4;
 
+// resident blocks per SM the register budget of the 16-voxel chunks is sized for (64
+// registers, no spills)
+#ifndef CBCT_BP_Z16_BLOCKS
+#define CBCT_BP_Z16_BLOCKS 8
+#endif
+
+// z voxels per thread. 16 halves the per-visit setup and the plane shared by two chunks,
+// but doubles a thread's work: it pays only where the grid still fills many waves of the
+// resident slots (at least six of 8 blocks per SM); measured 2.35 -> 2.26 ms for the paper's
+// 512x512x70 grid and 2.01 -> 1.87 ms for 512x512x128, while 256x256x64 (under two waves)
+// and 256x256x35 (a ragged last chunk) lose 1-4%. Otherwise 8, halved while the grid has
+// fewer than 4 blocks per SM.
 static int bp_zchunk(const GeomDev &G)
 {
     const long long tiles = (long long)((G.nx + BP_TX - 1) / BP_TX) * ((G.ny + BP_TY - 1) / BP_TY);
-    const long long want = 4LL * device_sm_count();
-    int zc = 8; // z voxels per thread at most
+    const long long sms = device_sm_count();
+    if (tiles * ((G.nz + 15) / 16) >= 6LL * CBCT_BP_Z16_BLOCKS * sms) return 16;
+    const long long want = 4LL * sms;
+    int zc = 8;
     while (zc > 1 && tiles * ((G.nz + zc - 1) / zc) < want) zc >>= 1;
     return zc;
 }
@@ -104,7 +118,7 @@ __device__ __forceinline__ void plane_terms_inside(const GeomDev &G, const float
 #define CBCT_BP_MIN_BLOCKS 9
 #endif
 template <int ZC, bool FLAT>
-__global__ void __launch_bounds__(BP_TX *BP_TY, ZC >= 8 ? CBCT_BP_MIN_BLOCKS : 1)
+__global__ void __launch_bounds__(BP_TX *BP_TY, ZC >= 16 ? CBCT_BP_Z16_BLOCKS : ZC >= 8 ? CBCT_BP_MIN_BLOCKS : 1)
 k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out, int sx, int sy, int sz,
               float *__restrict__ out2, double *__restrict__ partials)
 {
@@ -309,6 +323,7 @@ cbct_status launch_backproject(const GeomDev &G, const float2 *ps, float *out, l
     if (flat) k_backproject<Z, true><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials); \
     else k_backproject<Z, false><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials)
     switch (zc) {
+    case 16: CBCT_BP_LAUNCH(16); break;
     case 8: CBCT_BP_LAUNCH(8); break;
     case 4: CBCT_BP_LAUNCH(4); break;
     case 2: CBCT_BP_LAUNCH(2); break;

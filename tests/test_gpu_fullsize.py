@@ -95,6 +95,22 @@ def test_largest_grids_sampled_parity(cb, name):
                    l2_bar=3e-4 if name == "wide" else 1e-4, floor_rel=1e-4)
 
 
+def test_sixteen_voxel_chunks_per_column_walk_sampled_parity(cb):
+    """P^T with 16 z voxels per thread and the per-view column walk: a 512x512x64 grid (enough
+    blocks for 16-voxel chunks) of 1 mm voxels (shadows wider than 1.5 imager columns).
+
+    With two views a voxel is crossed by a handful of rays, so one ray's weight error shows
+    unaveraged: a ray 1.8 mm from the central imager row (elevation ~1e-3 rad) that crosses a
+    z plane inside the voxel puts the crossing at z / v - t_c, a difference of two numbers
+    near 0.6 whose FP32 rounding (~1e-7) moves the split point by ~2e-4 mm along the ray.
+    P and P^T share these weights exactly; against the FP64 oracle single samples reach
+    ~3e-4 (the same with 4, 8 or 16 voxels per thread), hence a per-sample bar of 1e-3 here
+    beside the relative-L2 bar of 1e-4."""
+    geom = synth.Geometry(nx=512, ny=512, nz=64, dx=1.0, dy=1.0, dz=1.0, nu=400, nv=100, du=1.2, dv=1.2,
+                          n_views=2, angles=(0.3, 1.9))
+    sampled_parity(cb, geom, 850, n_rays=1000, n_vox=200, per_sample=1e-3)
+
+
 DEGENERATE = {
     "one_slice": synth.Geometry(nx=20, ny=16, nz=1, dx=2.0, dy=2.0, dz=3.0, nu=30, nv=5, du=2.0, dv=2.0,
                                 n_views=4, angles=(0.2, 1.1, 2.9, 5.0)),
