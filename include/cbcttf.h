@@ -97,8 +97,8 @@ typedef struct {
  * (its transverse half-diagonal below both sad and sdd - sad). Sizes are limited to
  * nx + ny <= 4096, nz <= 1024, nx*ny*nz < 2^31 voxels and n_views*nv*nu < 2^31 pixels,
  * and jointly by the projector's shared memory per block, about
- * 16 (nx + ny) + 204 nz bytes <= 200 KiB (nz <= 918 at nx + ny = 1024, nz <= 677 at
- * nx + ny = 4096); a larger grid gives UNSUPPORTED.
+ * 16 (nx + ny) + 140 nz bytes <= 200 KiB (it binds above nx + ny = 3806 for nz = 1024;
+ * nz <= 990 at nx + ny = 4096); a larger grid gives UNSUPPORTED.
  * Synchronous. Errors: INVALID_ARG, UNSUPPORTED, OUT_OF_MEMORY, CUDA.
  */
 cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct_geometry **out);

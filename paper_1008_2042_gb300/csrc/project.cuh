@@ -43,12 +43,12 @@ static inline int seg_offset(const GeomDev &G) { return ((G.nx + G.ny + 2 + 3) /
 // projector reads has at least 16 bytes of slack after it (PROJECT_VOLUME_SLACK).
 static inline int line_pitch(int nz) { return ((nz + 6 + 3) / 4) * 4; }
 
-// shared memory: per segment (end tau, column offset, (line offset, length)); then two
-// staged groups of z-lines, whose space first holds phase 1's crossing lists; then the
+// shared memory: per segment (end tau, column offset, (line offset, length)); then the
+// staged z-lines of one group, whose space first holds phase 1's crossing lists; then the
 // group's per-slab prefix table and two rows of running per-slab totals
 static inline size_t line_region(const GeomDev &G, int sg)
 {
-    const size_t lines = 2 * (size_t)sg * line_pitch(G.nz), lists = (size_t)seg_offset(G);
+    const size_t lines = (size_t)sg * line_pitch(G.nz), lists = (size_t)seg_offset(G);
     return lines > lists ? lines : lists;
 }
 

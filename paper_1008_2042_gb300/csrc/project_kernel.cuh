@@ -80,10 +80,10 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
     float2 *sSeg = reinterpret_cast<float2 *>(sCol + cap); // (line offset bits, length) of segment j
     const int pitch = ((G.nz + 6 + 3) / 4) * 4;            // floats per staged line
     const int quads = pitch / 4;                           // 16-byte pieces per line slot
-    float *sLine = reinterpret_cast<float *>(sSeg + cap);  // two staged groups of z-lines
+    float *sLine = reinterpret_cast<float *>(sSeg + cap);  // the staged z-lines of one group
     float *sA = sLine;                                     // phase 1: x-plane crossings, in ray order
     float *sB = sA + (G.nx + 1);                           // phase 1: y-plane crossings
-    const int lregion = max(2 * SG * pitch, ((G.nx + G.ny + 2 + 3) / 4) * 4);
+    const int lregion = max(SG * pitch, ((G.nx + G.ny + 2 + 3) / 4) * 4);
     constexpr int TPITCH = SG + 1;                         // odd: the build's threads (slabs) hit distinct banks
     float *sTab = sLine + lregion;                         // [nz][SG + 1] per-slab prefix table
     float *sBase = sTab + G.nz * TPITCH;                   // [2][nz] running per-slab totals
@@ -216,9 +216,10 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
             }
         }
     } else if (hit) {
-        // Per group of SG segments: stage the z-lines of its columns (16-byte cp.async,
-        // one group ahead), build once for the block the per-slab prefix table over the
-        // group's columns,
+        // Per group of SG segments: stage the z-lines of its columns (16-byte cp.async into
+        // one buffer: a second buffer to copy the next group ahead would cost a resident
+        // block, which hides more latency than the early copy), build once for the block the
+        // per-slab prefix table over the group's columns,
         //     T[k][u] = sum_{u' < u} f(column u', slab k) * length(u'),   u = 0..SG,
         // and let every row add T[k][u1] - T[k][u0] for each run of whole columns it
         // spends in slab k. Only the columns in which a row crosses a z plane are split,
@@ -229,8 +230,8 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
         // thread tid takes c = tid, tid + nthr, ... (the same slots for every group)
         const int u_0 = tid / quads, i_0 = tid - u_0 * quads;
         const int du = nthr / quads, di = nthr - du * quads;
-        auto fill = [&](int chunk, int buf) {
-            float *dst = sLine + buf * SG * pitch;
+        auto fill = [&](int chunk) {
+            float *dst = sLine;
             const int *col = sCol + chunk * SG;
             for (int u = u_0, i = i_0; u < SG;) {
                 const int c0 = col[u];
@@ -254,14 +255,14 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
         };
         float E[R] = {0.0f, 0.0f}; // running total where each row's current run starts
         for (int k = tid; k < G.nz; k += nthr) sBase[k] = 0.0f; // published by the first barrier
-        fill(0, 0);
         float g0 = tau_in;
         for (int ch = 0; ch < nchunk; ++ch) {
             const int j = ch * SG;
+            if (ch) __syncthreads(); // every thread is done with the previous group's lines
+            fill(ch);
             cp_async_wait<0>();
-            __syncthreads(); // also: every thread is done with the previous group
-            if (ch + 1 < nchunk) fill(ch + 1, (ch + 1) & 1);
-            const float *lines = sLine + (ch & 1) * SG * pitch;
+            __syncthreads();
+            const float *lines = sLine;
             // The group's prefix table. With threads to spare each slab's running sum is
             // split into two chains of SG / 2 columns computed side by side; the second
             // half's entries then hold sums from column SG / 2 on, and tab() adds the

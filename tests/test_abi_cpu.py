@@ -62,8 +62,8 @@ def test_invalid_geometry_is_rejected_before_device_work(lib, bad):
     assert lib.cbct_last_error()
 
 
-@pytest.mark.parametrize("nx,ny,nz,ok", [(512, 512, 918, True), (512, 512, 919, False),
-                                         (64, 4032, 677, True), (64, 4032, 678, False)])
+@pytest.mark.parametrize("nx,ny,nz,ok", [(512, 512, 1024, True), (64, 3742, 1024, True), (64, 3743, 1024, False),
+                                         (64, 4032, 990, True), (64, 4032, 991, False)])
 def test_grids_beyond_the_projectors_shared_memory_are_unsupported(lib, nx, ny, nz, ok):
     """Largest grids: accepted up to the projector's shared-memory limit, UNSUPPORTED past
     it, before any device work (ok=True cases stop at the device allocation here)."""

@@ -80,8 +80,8 @@ def test_paper_scale_adjoint_identity(cb):
 
 
 LARGEST = {
-    # nz at the projector's shared-memory limit for nx + ny = 512 (16-column groups)
-    "tall": synth.Geometry(nx=256, ny=256, nz=950, dx=1.0, dy=1.0, dz=0.2, nu=384, nv=200, du=1.5, dv=1.5,
+    # nz at its limit (1024; the projector's shared memory would allow 1398 at nx + ny = 512)
+    "tall": synth.Geometry(nx=256, ny=256, nz=1024, dx=1.0, dy=1.0, dz=0.2, nu=384, nv=200, du=1.5, dv=1.5,
                            n_views=3, angles=(0.1, 1.7, 4.0)),
     # nx + ny at its limit (4096): the longest transverse traces
     "wide": synth.Geometry(nx=64, ny=4032, nz=16, dx=0.2, dy=0.2, dz=1.0, nu=600, nv=24, du=1.6, dv=1.5,

@@ -129,11 +129,11 @@ def test_project_group_choice(cb, forced_group):
     with cb.Geometry(big) as g:
         forced_group(0)
         a = cb.project_group(g, 0)
-        forced_group(96)  # 96 columns of 950-voxel lines exceed the shared memory
+        forced_group(96)  # 96 columns of 1024-voxel lines exceed the shared memory
         assert cb.project_group(g, 0) == a
 
 
-LARGEST_NZ = synth.Geometry(nx=256, ny=256, nz=950, dx=1.0, dy=1.0, dz=0.2, nu=64, nv=40, du=1.5, dv=1.5,
+LARGEST_NZ = synth.Geometry(nx=256, ny=256, nz=1024, dx=1.0, dy=1.0, dz=0.2, nu=64, nv=40, du=1.5, dv=1.5,
                             n_views=2, angles=(0.1, 1.7))
 
 
