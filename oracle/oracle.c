@@ -723,8 +723,10 @@ void o_cgls_storage(const og_geom *g, const double *y, double *x, int n_iter, do
  *   v = f^(k) + (t^(k-1) - 1) / t^(k) (f^(k) - f^(k-1));   [momentum = 0: v = f^(k), i.e. A1]
  *   f^(k+1) = CGLS[v];  f^(k+1) <- D^T T_mu D f^(k+1);  f^(k+1) <- H f^(k+1)  [if positivity];
  *   t^(k+1) = (1 + sqrt(1 + 4 t^(k)^2)) / 2.
- * storage selects the CGLS variant above. Parity of the iteration as a whole is pinned
- * only through special cases (tests).
+ * storage selects the CGLS variant above. Parity unpinned for the momentum schedule and
+ * the iteration as a whole: the tests pin only special cases (mu = 0 reaches the least-
+ * squares solution with and without momentum, a consistent positive constant is a fixed
+ * point, momentum converges faster than A1).
  */
 static void a2_impl(const og_geom *g, const double *y, double mu, int n_outer, int n_cgls, int positivity,
                     int momentum, int storage, double *f)
@@ -833,7 +835,9 @@ void o_restrict(int nx, int ny, int nz, double dx, double dy, double dz, const d
  * voxels per axis at 2^l times the spacing, same centre; the imager and y are the same
  * on every level. Start with f = 0 on the coarsest grid, run A2 there, prolong the
  * result as the initial guess of the next finer grid, and so on. iters[] lists the A2
- * iteration counts coarsest first.
+ * iteration counts coarsest first. Parity unpinned beyond the special cases the tests pin
+ * (one level equals A2 on that grid; a second level starts from the prolonged coarse
+ * result; prolongation is exact on linear functions).
  */
 static void reconstruct_impl(const og_geom *g, const double *y, double mu, int levels, const int *iters,
                              int n_cgls, int positivity, int momentum, int storage, double *f_out)
