@@ -77,7 +77,7 @@ def _load():
                 "o_cgls": (None, [G, _P, _P, ctypes.c_int, _P]),
                 "o_cgls_storage": (None, [G, _P, _P, ctypes.c_int, _P, ctypes.c_int]),
                 "o_round_storage": (None, [ctypes.c_long, _P, ctypes.c_int]),
-                "o_a2": (None, [G, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+                "o_a2": (None, [G, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
                 "o_prolong": (None, [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [_P] + [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [_P]),
                 "o_restrict": (None, [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [_P] + [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [_P]),
                 "o_reconstruct": (None, [G, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
@@ -271,14 +271,17 @@ def cgls(geom, y, x0, n_iter, return_resid=False, storage=0):
     return (x, res) if return_resid else x
 
 
-def a2(geom, y, mu, n_outer, n_cgls=3, positivity=True, momentum=True, f0=None):
-    """Algorithm A2 (A1 with momentum=False) on one grid from f0 (default 0)."""
+def a2(geom, y, mu, n_outer, n_cgls=3, positivity=True, momentum=True, f0=None,
+       return_coefficients=False):
+    """Algorithm A2 (A1 with momentum=False) on one grid from f0 (default 0). With
+    return_coefficients, also the momentum coefficient each iteration applied."""
     lib = _load(); gh = _GeomHolder(geom)
     y = _f64(y, geom.proj_shape)
     f = np.zeros(geom.vol_shape) if f0 is None else _f64(f0, geom.vol_shape).copy()
+    coef = np.full(max(int(n_outer), 1), np.nan)
     lib.o_a2(gh.ref(), _ptr(y), float(mu), int(n_outer), int(n_cgls), int(bool(positivity)),
-             int(bool(momentum)), _ptr(f))
-    return f
+             int(bool(momentum)), _ptr(f), _ptr(coef))
+    return (f, coef[:int(n_outer)]) if return_coefficients else f
 
 
 def prolong(fc, coarse_spacing, fine_shape, fine_spacing):
@@ -316,14 +319,4 @@ def reconstruct(geom, y, mu, levels, iters, n_cgls=3, positivity=True, momentum=
     out = np.empty(geom.vol_shape)
     lib.o_reconstruct_storage(gh.ref(), _ptr(y), float(mu), int(levels), it, int(n_cgls),
                               int(bool(positivity)), int(bool(momentum)), _storage(storage), _ptr(out))
-    return out
-
-
-def a2_momentum_coefficients(n: int):
-    """The A2 coefficients (t^(k-1) - 1) / t^(k) for k = 0..n-1 (host restatement used
-    by tests to describe the schedule; the C iteration computes its own)."""
-    t_prev, t, out = 1.0, 1.0, []
-    for _ in range(n):
-        out.append((t_prev - 1.0) / t)
-        t_prev, t = t, 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
     return out

@@ -146,3 +146,118 @@ def krylov_lsq(A, y, x0, n_iter):
     K = np.stack(vecs, axis=1)
     c, *_ = np.linalg.lstsq(A @ K, r0, rcond=None)
     return x0 + K @ c
+
+
+# ---------------------------------------------------------------------------------------
+# Dense restatement of the tight frame, Algorithm A2 and the multigrid cascade
+# ---------------------------------------------------------------------------------------
+
+# The paper's piecewise-linear filters (Section 2.1), taps at offsets -1, 0, +1.
+_TAPS = (np.array([1.0, 2.0, 1.0]) / 4.0,
+         np.sqrt(2.0) / 4.0 * np.array([1.0, 0.0, -1.0]),
+         np.array([-1.0, 2.0, -1.0]) / 4.0)
+
+
+def filter_matrix(n: int, l: int) -> np.ndarray:
+    """n x n periodic convolution matrix of filter l: (H f)[x] = sum_a h_l[a] f[x - a]."""
+    H = np.zeros((n, n))
+    for a, h in zip((-1, 0, 1), _TAPS[l]):
+        for x in range(n):
+            H[x, (x - a) % n] += h
+    return H
+
+
+def frame_analysis(f: np.ndarray) -> np.ndarray:
+    """W f as 27 channels (27, nz, ny, nx), channel i = l + 3m + 9n: the 1-D filter
+    matrices applied along x (l), y (m) and z (n)."""
+    nz, ny, nx = f.shape
+    out = np.empty((27,) + f.shape)
+    for i in range(27):
+        l, m, n = i % 3, (i // 3) % 3, i // 9
+        out[i] = np.einsum("zc,yb,xa,cba->zyx", filter_matrix(nz, n), filter_matrix(ny, m),
+                           filter_matrix(nx, l), f)
+    return out
+
+
+def frame_synthesis(alpha: np.ndarray) -> np.ndarray:
+    """W^T alpha: the transposed filter matrices applied per channel and summed."""
+    _, nz, ny, nx = alpha.shape
+    out = np.zeros(alpha.shape[1:])
+    for i in range(27):
+        l, m, n = i % 3, (i // 3) % 3, i // 9
+        out += np.einsum("cz,by,ax,cba->zyx", filter_matrix(nz, n), filter_matrix(ny, m),
+                         filter_matrix(nx, l), alpha[i])
+    return out
+
+
+def shrink(alpha: np.ndarray, mu: float) -> np.ndarray:
+    """Eq. (2): keep the low-pass channel, scale the 26 high-pass coefficients of each
+    voxel by max(1 - mu / ||alpha_h||, 0) (factor 0 where the norm is 0)."""
+    nrm = np.sqrt((alpha[1:] ** 2).sum(axis=0))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        scale = np.where(nrm > mu, 1.0 - mu / np.where(nrm > 0, nrm, 1.0), 0.0)
+    out = alpha.copy()
+    out[1:] *= scale
+    return out
+
+
+def a2_dense(A, y, shape, mu, n_outer, n_cgls=3, positivity=True, momentum=True, f0=None):
+    """Algorithm A2 (Section 2.1) with the dense system matrix A: momentum point, n_cgls
+    CGLS updates, frame shrinkage, positivity, then the t recurrence
+    t <- (1 + sqrt(1 + 4 t^2)) / 2 from t^(0) = t^(-1) = 1."""
+    y = np.asarray(y, dtype=np.float64).ravel()
+    f = np.zeros(shape) if f0 is None else np.array(f0, dtype=np.float64)
+    f_prev = f.copy()
+    t_prev = t = 1.0
+    for _ in range(n_outer):
+        c = (t_prev - 1.0) / t if momentum else 0.0
+        v = f + c * (f - f_prev)
+        x = cgls_dense(A, y, v.ravel(), n_cgls).reshape(shape)
+        x = frame_synthesis(shrink(frame_analysis(x), mu))
+        if positivity:
+            x = np.where(x < 0.0, 0.0, x)
+        f_prev, f = f, x
+        t_prev, t = t, 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
+    return f
+
+
+def interpolation_matrix(nc: int, hc: float, nf: int, hf: float) -> np.ndarray:
+    """nf x nc linear interpolation from coarse voxel centres to fine voxel centres along
+    one axis (both grids centred on 0), the position clamped to the coarse centres' span."""
+    xc = -0.5 * nc * hc + (np.arange(nc) + 0.5) * hc
+    xf = -0.5 * nf * hf + (np.arange(nf) + 0.5) * hf
+    T = np.zeros((nf, nc))
+    for i, x in enumerate(xf):
+        if nc == 1 or x <= xc[0]:
+            T[i, 0] = 1.0
+        elif x >= xc[-1]:
+            T[i, -1] = 1.0
+        else:
+            j = int(np.searchsorted(xc, x, side="right")) - 1
+            w = (x - xc[j]) / (xc[j + 1] - xc[j])
+            T[i, j] += 1.0 - w
+            T[i, j + 1] += w
+    return T
+
+
+def reconstruct_dense(geom, y, mu, levels, iters, n_cgls=3, positivity=True, momentum=True):
+    """The multigrid cascade of Section 2.2.3 with dense matrices: level l has
+    ceil(n / 2^l) voxels per axis at 2^l times the spacing (same centre, same imager and
+    y); A2 from 0 on the coarsest grid, each result interpolated (per axis, trilinear) to
+    start the next finer grid. iters is coarsest first."""
+    y = np.asarray(y, dtype=np.float64).ravel()
+    f = None
+    prev = None
+    for lev in range(levels - 1, -1, -1):
+        gl = geom.level(lev)
+        shape = gl.vol_shape
+        f0 = None
+        if f is not None:
+            Tz = interpolation_matrix(prev.nz, prev.dz, gl.nz, gl.dz)
+            Ty = interpolation_matrix(prev.ny, prev.dy, gl.ny, gl.dy)
+            Tx = interpolation_matrix(prev.nx, prev.dx, gl.nx, gl.dx)
+            f0 = np.einsum("zc,yb,xa,cba->zyx", Tz, Ty, Tx, f)
+        f = a2_dense(system_matrix(gl), y, shape, mu, iters[levels - 1 - lev], n_cgls,
+                     positivity, momentum, f0)
+        prev = gl
+    return f

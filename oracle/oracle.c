@@ -723,13 +723,16 @@ void o_cgls_storage(const og_geom *g, const double *y, double *x, int n_iter, do
  *   v = f^(k) + (t^(k-1) - 1) / t^(k) (f^(k) - f^(k-1));   [momentum = 0: v = f^(k), i.e. A1]
  *   f^(k+1) = CGLS[v];  f^(k+1) <- D^T T_mu D f^(k+1);  f^(k+1) <- H f^(k+1)  [if positivity];
  *   t^(k+1) = (1 + sqrt(1 + 4 t^(k)^2)) / 2.
- * storage selects the CGLS variant above. Parity unpinned for the momentum schedule and
- * the iteration as a whole: the tests pin only special cases (mu = 0 reaches the least-
- * squares solution with and without momentum, a consistent positive constant is a fixed
- * point, momentum converges faster than A1).
+ * storage selects the CGLS variant above. coef (optional, n_outer entries) receives the
+ * momentum coefficient each iteration applied.
+ * Pinned by: the coefficients against hand-evaluated values of the recurrence; with the
+ * data step removed (n_cgls = 0, H off) the iterates against the momentum-accelerated
+ * shrinkage sequence built from those values; mu = 0 reaches the least-squares solution
+ * with and without momentum; a consistent positive constant is a fixed point; momentum
+ * converges faster than A1; an independent dense-matrix restatement (tests).
  */
 static void a2_impl(const og_geom *g, const double *y, double mu, int n_outer, int n_cgls, int positivity,
-                    int momentum, int storage, double *f)
+                    int momentum, int storage, double *f, double *coef)
 {
     long N = (long)g->nx * g->ny * g->nz;
     double *fprev = (double *)malloc(sizeof(double) * N);
@@ -739,6 +742,7 @@ static void a2_impl(const og_geom *g, const double *y, double mu, int n_outer, i
     double t_prev = 1.0, t = 1.0;
     for (int k = 0; k < n_outer; k++) {
         double c = momentum ? (t_prev - 1.0) / t : 0.0;
+        if (coef) coef[k] = c;
         for (long j = 0; j < N; j++) x[j] = f[j] + c * (f[j] - fprev[j]);
         cgls_impl(g, y, x, n_cgls, NULL, storage);
         o_tf_analyze(g->nx, g->ny, g->nz, x, alpha);
@@ -755,9 +759,9 @@ static void a2_impl(const og_geom *g, const double *y, double mu, int n_outer, i
 }
 
 void o_a2(const og_geom *g, const double *y, double mu, int n_outer, int n_cgls, int positivity,
-          int momentum, double *f)
+          int momentum, double *f, double *coef)
 {
-    a2_impl(g, y, mu, n_outer, n_cgls, positivity, momentum, 0, f);
+    a2_impl(g, y, mu, n_outer, n_cgls, positivity, momentum, 0, f, coef);
 }
 
 /*
@@ -802,6 +806,8 @@ void o_prolong(int cnx, int cny, int cnz, double cdx, double cdy, double cdz, co
  * Restriction (fine -> coarse): each coarse voxel takes the mean of the fine voxels
  * whose centres lie inside it (both grids centred on the origin); a coarse voxel with no
  * such fine voxel is 0. Not used by the cascadic multigrid; kept for tests.
+ * Pinned by: constants; a linear function, whose mean over the fine centres inside a
+ * coarse voxel is its value at their centroid, on aligned and ragged grids (tests).
  */
 void o_restrict(int nx, int ny, int nz, double dx, double dy, double dz, const double *ff,
                 int cnx, int cny, int cnz, double cdx, double cdy, double cdz, double *fc)
@@ -835,9 +841,10 @@ void o_restrict(int nx, int ny, int nz, double dx, double dy, double dz, const d
  * voxels per axis at 2^l times the spacing, same centre; the imager and y are the same
  * on every level. Start with f = 0 on the coarsest grid, run A2 there, prolong the
  * result as the initial guess of the next finer grid, and so on. iters[] lists the A2
- * iteration counts coarsest first. Parity unpinned beyond the special cases the tests pin
- * (one level equals A2 on that grid; a second level starts from the prolonged coarse
- * result; prolongation is exact on linear functions).
+ * iteration counts coarsest first.
+ * Pinned by: one level equals A2 on that grid; a second level starts from the prolonged
+ * coarse result; prolongation is exact on linear functions; an independent dense-matrix
+ * restatement of the whole cascade on small grids (tests).
  */
 static void reconstruct_impl(const og_geom *g, const double *y, double mu, int levels, const int *iters,
                              int n_cgls, int positivity, int momentum, int storage, double *f_out)
@@ -856,7 +863,7 @@ static void reconstruct_impl(const og_geom *g, const double *y, double mu, int l
                       gl.nx, gl.ny, gl.nz, gl.dx, gl.dy, gl.dz, f);
             free(fc);
         }
-        a2_impl(&gl, y, mu, iters[levels - 1 - lev], n_cgls, positivity, momentum, storage, f);
+        a2_impl(&gl, y, mu, iters[levels - 1 - lev], n_cgls, positivity, momentum, storage, f, NULL);
         fc = f;
         prev = gl;
     }

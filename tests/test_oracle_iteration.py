@@ -1,12 +1,16 @@
 """Pins of the oracle's CGLS (Appendix 1), Algorithm A2 (Section 2.1) and the multigrid
 transfer operators (Section 2.2.3) against exact least-squares solutions, invariants and
 special cases."""
+import os
+
 import numpy as np
 import pytest
 
 import oracle
 import synth
 from oracle import dense
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 def _tiny_geom(n_views=6):
@@ -88,10 +92,79 @@ def test_a2_momentum_accelerates_a1():
     assert res[True] < 0.7 * res[False], res
 
 
-def test_a2_momentum_schedule():
-    c = oracle.a2_momentum_coefficients(5)
-    assert c[0] == 0.0 and c[1] == 0.0          # t^(0) = t^(-1) = 1
-    assert 0.0 < c[2] < c[3] < c[4] < 1.0
+def _golden_momentum():
+    """(t^(k), c_k) for k = 0..7 from the golden file (hand-evaluated recurrence)."""
+    rows = []
+    with open(os.path.join(GOLDEN, "a2_momentum.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, t, c = line.split()
+                rows.append((int(k), float(t), float(c)))
+    assert [r[0] for r in rows] == list(range(len(rows)))
+    return np.array([r[1] for r in rows]), np.array([r[2] for r in rows])
+
+
+def test_a2_momentum_schedule_matches_hand_evaluated_recurrence():
+    """Section 2.1, Algorithm A2: the coefficient each iteration of the C iteration
+    applies equals (t^(k-1) - 1) / t^(k) of the paper's recurrence, evaluated by hand."""
+    _, c_ref = _golden_momentum()
+    geom = _small_geom()
+    y = oracle.project(geom, np.full(geom.vol_shape, 0.01))
+    _, c = oracle.a2(geom, y, 5e-4, len(c_ref), n_cgls=1, return_coefficients=True)
+    assert np.abs(c - c_ref).max() <= 1e-15, (c, c_ref)
+    _, c1 = oracle.a2(geom, y, 5e-4, 4, n_cgls=1, momentum=False, return_coefficients=True)
+    assert not c1.any()  # A1: no momentum
+
+
+def test_a2_applies_the_momentum_point_as_stated():
+    """With the data step removed (no CGLS update) and H off, A2 is the accelerated
+    shrinkage iteration f^(k+1) = W^T T_mu W (f^(k) + c_k (f^(k) - f^(k-1))), f^(-1) =
+    f^(0); built here from the pinned frame operators and the golden c_k, so a shifted
+    coefficient index or a sign error in the momentum point fails."""
+    _, c_ref = _golden_momentum()
+    geom = _small_geom()
+    rng = np.random.default_rng(11)
+    f0 = rng.uniform(0.0, 0.04, geom.vol_shape)
+    mu = 4e-3
+    y = np.zeros(geom.proj_shape)
+    n = 6
+    f, c = oracle.a2(geom, y, mu, n, n_cgls=0, positivity=False, f0=f0, return_coefficients=True)
+    prev, cur = f0.copy(), f0.copy()
+    for k in range(n):
+        v = cur + c_ref[k] * (cur - prev)
+        prev, cur = cur, oracle.tf_synthesize(oracle.tf_shrink(oracle.tf_analyze(v), mu))
+    assert np.abs(f - cur).max() <= 1e-13 * np.abs(cur).max()
+    # the momentum terms matter here: without them the result differs
+    f_a1 = oracle.a2(geom, y, mu, n, n_cgls=0, positivity=False, f0=f0, momentum=False)
+    assert np.abs(f_a1 - cur).max() > 1e-6 * np.abs(cur).max()
+
+
+@pytest.mark.parametrize("momentum,positivity", [(True, True), (False, True), (True, False)])
+def test_a2_equals_dense_restatement(momentum, positivity):
+    """The C iteration against an independent dense-matrix restatement (slab-clipped
+    system matrix, per-axis circulant frame filters, dense CGLS)."""
+    geom = _small_geom()
+    f_true = synth.voxelize(geom, synth.random_ellipsoids(geom, 21, n=4, vmax=0.04))
+    y = synth.noisy_line_integrals(oracle.project(geom, f_true), 1e4, 22)
+    A = dense.system_matrix(geom)
+    for mu in (0.0, 2e-3):
+        f = oracle.a2(geom, y, mu, 5, n_cgls=2, positivity=positivity, momentum=momentum)
+        ref = dense.a2_dense(A, y, geom.vol_shape, mu, 5, 2, positivity, momentum)
+        assert np.linalg.norm(f - ref) <= 1e-12 * np.linalg.norm(ref), (mu, np.linalg.norm(f - ref))
+
+
+@pytest.mark.parametrize("shape,levels,iters", [((8, 8, 8), 3, [2, 3, 2]), ((10, 16, 12), 2, [3, 2])])
+def test_multigrid_equals_dense_restatement(shape, levels, iters):
+    """The whole cascade of Section 2.2.3 (coarsest first, prolongation between levels,
+    odd coarse sizes included) against the dense restatement."""
+    nz, ny, nx = shape
+    geom = synth.Geometry(nx=nx, ny=ny, nz=nz, dx=4.0, dy=4.0, dz=4.0, nu=16, nv=12, du=4.0, dv=4.0,
+                          n_views=6, angles=tuple(0.3 + 2 * np.pi * np.arange(6) / 6))
+    f_true = synth.voxelize(geom, synth.random_ellipsoids(geom, 31, n=4, vmax=0.04))
+    y = synth.noisy_line_integrals(oracle.project(geom, f_true), 1e4, 32)
+    out = oracle.reconstruct(geom, y, 1e-3, levels, iters)
+    ref = dense.reconstruct_dense(geom, y, 1e-3, levels, iters)
+    assert np.linalg.norm(out - ref) <= 1e-12 * np.linalg.norm(ref), np.linalg.norm(out - ref)
 
 
 def test_a2_shrinkage_lowers_frame_sparsity_measure():
@@ -130,6 +203,29 @@ def test_restrict_of_constant_and_prolong_of_restrict_shapes():
     ff = np.full((7, 9, 10), 1.25)
     fc = oracle.restrict(ff, (1.0, 1.0, 1.0), (4, 5, 5), (2.0, 2.0, 2.0))
     assert np.abs(fc - 1.25).max() < 1e-15
+
+
+def test_restrict_of_linear_function_on_aligned_grids():
+    """Each coarse voxel holds 2x2x2 fine centres whose centroid is its own centre, so a
+    linear function restricts to its values at the coarse centres."""
+    lin = lambda z, y, x: 0.3 + 0.1 * x - 0.2 * y + 0.05 * z
+    fshape, fs = (6, 8, 10), (1.0, 1.5, 2.0)      # (nz, ny, nx); spacings (dx, dy, dz)
+    cshape, cs = (3, 4, 5), (2.0, 3.0, 4.0)
+    c = lambda n, h: -n * h / 2 + (np.arange(n) + 0.5) * h
+    ff = lin(c(fshape[0], fs[2])[:, None, None], c(fshape[1], fs[1])[None, :, None], c(fshape[2], fs[0])[None, None, :])
+    ref = lin(c(cshape[0], cs[2])[:, None, None], c(cshape[1], cs[1])[None, :, None], c(cshape[2], cs[0])[None, None, :])
+    assert np.abs(oracle.restrict(ff, fs, cshape, cs) - ref).max() < 1e-14
+
+
+def test_restrict_of_linear_function_on_a_ragged_grid():
+    """7 fine voxels of 1 mm (centres -3..3) under 4 coarse voxels of 2 mm (boxes
+    [-4,-2), [-2,0), [0,2), [2,4)): the coarse voxels hold the centres {-3}, {-2,-1},
+    {0,1}, {2,3}, whose means are -3, -1.5, 0.5, 2.5. A linear function of x restricts
+    to its values there; a shifted or reversed coarse index fails."""
+    x = np.arange(7) - 3.0
+    ff = np.broadcast_to(0.2 + 0.7 * x, (2, 2, 7)).copy()
+    fc = oracle.restrict(ff, (1.0, 1.0, 1.0), (1, 1, 4), (2.0, 2.0, 2.0))
+    assert np.abs(fc[0, 0] - (0.2 + 0.7 * np.array([-3.0, -1.5, 0.5, 2.5]))).max() < 1e-15
 
 
 def test_multigrid_single_level_equals_a2():
