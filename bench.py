@@ -222,6 +222,54 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------------------
+# Frame transforms against the HBM roofline
+# ---------------------------------------------------------------------------------------
+
+def time_frame_transforms(cb, geom, device, reps: int = 10, mu: float = MU):
+    """Device time of the public analysis W (cbct_tf_analyze) and shrink + synthesis
+    (cbct_tf_synthesize_shrink) on the workload's finest grid, FP32 and BF16 coefficients:
+    median of `reps` calls, each bracketed by CUDA events on the launching stream. The
+    coefficient array (1.98 GB in FP32, 0.99 GB in BF16) exceeds L2, so every call streams
+    it from HBM. Algorithmic bytes per voxel: W reads 4 and writes 27 coefficients, the
+    synthesis reads 27 coefficients and writes 4."""
+    import torch
+    peak = float(measured_peaks().get("hbm_gbs") or 6800.0)
+    stream = torch.cuda.current_stream()
+    n = geom.nx * geom.ny * geom.nz
+    gen = torch.Generator(device=device).manual_seed(5)
+    f = torch.rand(geom.vol_shape, device=device, generator=gen) * 0.04
+    out = torch.empty_like(f)
+    res = {}
+    for name, dt, es in (("f32", torch.float32, 4), ("bf16", torch.bfloat16, 2)):
+        alpha = torch.empty((27,) + tuple(geom.vol_shape), dtype=dt, device=device)
+        for op in ("analyze", "synthesize_shrink"):
+            def call():
+                if op == "analyze":
+                    cb.tf_analyze(f, out=alpha)
+                else:
+                    cb.tf_synthesize_shrink(alpha, mu, True, out=out)
+            call()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                call()
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            t = statistics.median(ms)
+            nbytes = n * (4 + 27 * es)
+            gbs = nbytes / (t / 1e3) / 1e9
+            res[f"{op}_{name}"] = {"ms": round(t, 4), "bytes": nbytes, "gbs": round(gbs, 1),
+                                    "frac": round(gbs / peak, 4)}
+        del alpha
+    res["peak_gbs"] = peak
+    res["peak_source"] = "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"
+    return res
+
+
+# ---------------------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the workload
 # ---------------------------------------------------------------------------------------
 
