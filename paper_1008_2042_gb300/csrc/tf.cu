@@ -120,99 +120,138 @@ k_tf_analyze(int n0, int n1, int n2, int chunk, const float *__restrict__ f, TA_
     }
 }
 
-constexpr int SA_PLANE = (TB + 2) * (TA + 2); // one channel of the haloed tile
-constexpr int SU_PLANE = (TB + 2) * TA;
-constexpr size_t TF_SYN_SMEM = sizeof(float) * (27 * SA_PLANE + 9 * SU_PLANE);
+// Planes per block along axis 2 (shrink + synthesis and the fused step): the split whose blocks fill whole
+// waves of the resident slots best, counting the two extra planes each block recomputes
+// at its start (a block's cost grows with chunk + 2).
+static int fused_chunk(long long tiles, int n2, int slots)
+{
+    int best = n2;
+    double best_eff = -1.0;
+    for (int nch = 1; nch <= n2; ++nch) {
+        const int chunk = (n2 + nch - 1) / nch;
+        if (nch > 1 && chunk == (n2 + nch - 2) / (nch - 1)) continue; // same split as nch - 1
+        const long long nb = tiles * ((n2 + chunk - 1) / chunk);
+        const long long waves = (nb + slots - 1) / slots;
+        const double eff = (double)n2 / ((double)((n2 + chunk - 1) / chunk) * (chunk + 2)) * (double)nb /
+                           ((double)waves * slots);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = chunk;
+        }
+    }
+    return best;
+}
+
+// ------------------------------------------------------------------------------------
+// Shrink + synthesis f = H(W^T T_mu alpha) of the public entry point.
+//
+// A warp covers 32 consecutive positions of one row along axis 0 (the 30 positions of the
+// tile plus one halo position on either side); a block stacks SY_ROWS + 2 such warps along
+// axis 1 (its SY_ROWS rows plus one halo row on either side) and marches along axis 2.
+// Every lane reads the 27 coefficients of its own position (coalesced 128-byte rows per
+// channel), the next plane's while the current one is computed, and shrinks them in
+// registers (Eq. (2)). The separable synthesis then splits each 3-tap sum into what a
+// position gives its neighbours: along axis 1 of the filter triple (a_0, a_1, a_2) at
+// position p, p + 1 receives a_0/4 + (sqrt(2)/4) a_1 - a_2/4, p itself (a_0 + a_2)/2 and
+// p - 1 a_0/4 - (sqrt(2)/4) a_1 - a_2/4. Axis 0 passes those shares between lanes with
+// two shuffles per channel group, axis 1 between warps through shared memory (one
+// barrier per plane, double buffered), and axis 2 between planes in registers.
+// HBM traffic: 27 coefficients read and one value written per voxel; the halo positions
+// (32/30 along axis 0, (SY_ROWS + 2)/SY_ROWS along axis 1) are re-read from L2.
+// ------------------------------------------------------------------------------------
+constexpr int SY_ROWS = 8;
+constexpr int SY_OUT = 30;                       // output positions per warp along axis 0
+constexpr int SY_WARPS = SY_ROWS + 2;
+constexpr int SY_THREADS = 32 * SY_WARPS;
+
+__device__ __forceinline__ float raw_to_float(float v) { return v; }
+__device__ __forceinline__ float raw_to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float raw_to_float(__half v) { return __half2float(v); }
+
+// shares of a filter triple (a0, a1, a2): to p + 1, to p, to p - 1
+__device__ __forceinline__ void syn_shares(float a0, float a1, float a2, float &up, float &mid, float &dn)
+{
+    const float q = 0.25f * (a0 - a2);
+    up = fmaf(R2_4, a1, q);
+    dn = fmaf(-R2_4, a1, q);
+    mid = 0.5f * (a0 + a2);
+}
 
 template <typename TA_T>
-__global__ void __launch_bounds__(TF_THREADS)
+__global__ void __launch_bounds__(SY_THREADS, 2)
 k_tf_synth_shrink(int n0, int n1, int n2, int chunk, const TA_T *__restrict__ alpha, float mu,
                   int positivity, float *__restrict__ f)
 {
-    extern __shared__ float sm[];
-    float *sa = sm;                   // [27][TB+2][TA+2]: shrunk coefficients of one plane
-    float *su = sm + 27 * SA_PLANE;   // [9][TB+2][TA]: after synthesis along axis 0
-    const int a0 = blockIdx.x * TA, b0 = blockIdx.y * TB;
+    __shared__ float s_up[2][SY_WARPS][3][32], s_dn[2][SY_WARPS][3][32];
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int a_out = blockIdx.x * SY_OUT;           // first output position along axis 0
+    const int b_out = blockIdx.y * SY_ROWS;          // first output row along axis 1
     const int c_begin = blockIdx.z * chunk;
     const int c_end = min(n2, c_begin + chunk);
     if (c_begin >= c_end) return;
-    const int tid = threadIdx.y * TA + threadIdx.x;
-    const int ta = threadIdx.x, tb = threadIdx.y;
     const size_t N = (size_t)n0 * n1 * n2;
-    const bool inside = a0 + ta < n0 && b0 + tb < n1;
+    const size_t plane = (size_t)n0 * n1;
+    const int pa = a_out + lane - 1, pb = b_out + w - 1; // this lane's position (unwrapped)
+    const size_t inplane = (size_t)wrapi(pb, n1) * n0 + wrapi(pa, n0);
+    const bool out_lane = lane >= 1 && lane <= SY_OUT && pa < n0;
+    const bool out_row = w >= 1 && w <= SY_ROWS && pb < n1;
 
-    // in-plane source offset of the (at most two) haloed-tile positions this thread loads
-    int off[2];
+    TA_T nxt[27];
+    auto fetch = [&](int c) {
+        const TA_T *src = alpha + (size_t)wrapi(c, n2) * plane + inplane;
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int pos = tid + k * TF_THREADS;
-        if (pos < SA_PLANE) {
-            const int r = pos / (TA + 2), q = pos - r * (TA + 2);
-            off[k] = wrapi(b0 + r - 1, n1) * n0 + wrapi(a0 + q - 1, n0);
-        } else {
-            off[k] = -1;
-        }
-    }
-    float w_m2[3] = {0.f, 0.f, 0.f}, w_m1[3] = {0.f, 0.f, 0.f}; // w_n at planes c'-2, c'-1
-    for (int cp = c_begin - 1; cp <= c_end; ++cp) {
-        const int cw = wrapi(cp, n2);
-        // 1. coefficients of plane cp on the haloed tile (the in-plane offsets are fixed)
-        {
-            const TA_T *src = alpha + (size_t)cw * n1 * n0;
-#pragma unroll 1
-            for (int k = 0; k < 2; ++k) {
-                if (off[k] >= 0) {
-                    const TA_T *p = src + off[k];
-                    float *d = sa + tid + k * TF_THREADS;
-#pragma unroll 9
-                    for (int ch = 0; ch < 27; ++ch) d[ch * SA_PLANE] = load_as_float(p + (size_t)ch * N);
-                }
-            }
-        }
-        __syncthreads();
-        // 2. vector shrinkage, Eq. (2): scale the 26 high-pass channels of every position
-        for (int pos = tid; pos < SA_PLANE; pos += TF_THREADS) {
-            float s2 = 0.0f;
+        for (int ch = 0; ch < 27; ++ch) nxt[ch] = src[(size_t)ch * N];
+    };
+    fetch(c_begin - 1);
+    float w_m2[3] = {0.f, 0.f, 0.f}, w_m1[3] = {0.f, 0.f, 0.f}; // axis-2 inputs at planes cp-2, cp-1
+    int buf = 0;
+    for (int cp = c_begin - 1; cp <= c_end; ++cp, buf ^= 1) {
+        float a[27];
 #pragma unroll
-            for (int ch = 1; ch < 27; ++ch) {
-                const float a = sa[ch * SA_PLANE + pos];
-                s2 = fmaf(a, a, s2);
-            }
-            const float nrm = sqrtf(s2);
-            const float scale = nrm > mu ? 1.0f - mu / nrm : 0.0f;
+        for (int ch = 0; ch < 27; ++ch) a[ch] = raw_to_float(nxt[ch]);
+        if (cp < c_end) fetch(cp + 1);
+        // vector shrinkage, Eq. (2)
+        float s2 = 0.0f;
 #pragma unroll
-            for (int ch = 1; ch < 27; ++ch) sa[ch * SA_PLANE + pos] *= scale;
+        for (int ch = 1; ch < 27; ++ch) s2 = fmaf(a[ch], a[ch], s2);
+        const float nrm = sqrtf(s2);
+        const float scale = nrm > mu ? 1.0f - mu / nrm : 0.0f;
+#pragma unroll
+        for (int ch = 1; ch < 27; ++ch) a[ch] *= scale;
+        // axis 0 (lanes): u[m + 3n] = sum over l and the lane's neighbours
+        float u[9];
+#pragma unroll
+        for (int mn = 0; mn < 9; ++mn) {
+            float up, mid, dn;
+            syn_shares(a[3 * mn], a[3 * mn + 1], a[3 * mn + 2], up, mid, dn);
+            u[mn] = __shfl_up_sync(0xffffffffu, up, 1) + mid + __shfl_down_sync(0xffffffffu, dn, 1);
         }
-        __syncthreads();
-        // 3. synthesis along axis 0: u_{mn} = sum_l, for TA x (TB+2) positions
-        for (int i = tid; i < 9 * SU_PLANE; i += TF_THREADS) {
-            const int mn = i / SU_PLANE, rem = i - mn * SU_PLANE;
-            const int r = rem / TA, q = rem - r * TA;
-            const float *b0p = sa + (3 * mn) * SA_PLANE + r * (TA + 2) + q; // l = 0
-            const float *b1p = b0p + SA_PLANE, *b2p = b1p + SA_PLANE;
-            su[i] = syn3(b0p[0], b0p[1], b0p[2], b1p[0], b1p[2], b2p[0], b2p[1], b2p[2]);
-        }
-        __syncthreads();
-        // 4. synthesis along axis 1: w_n = sum_m
-        float w[3];
+        // axis 1 (warps): shares of rows to the rows above and below through shared memory
+        float midn[3];
 #pragma unroll
         for (int n = 0; n < 3; ++n) {
-            const float *m0 = su + (3 * n + 0) * SU_PLANE + tb * TA + ta;
-            const float *m1 = m0 + SU_PLANE, *m2 = m1 + SU_PLANE;
-            w[n] = syn3(m0[0], m0[TA], m0[2 * TA], m1[0], m1[2 * TA], m2[0], m2[TA], m2[2 * TA]);
-        }
-        // 5. synthesis along axis 2 gives plane cp - 1
-        if (cp >= c_begin + 1 && inside) {
-            float out = syn3(w_m2[0], w_m1[0], w[0], w_m2[1], w[1], w_m2[2], w_m1[2], w[2]);
-            if (positivity && out < 0.0f) out = 0.0f;
-            f[((size_t)(cp - 1) * n1 + (b0 + tb)) * n0 + (a0 + ta)] = out;
-        }
-#pragma unroll
-        for (int n = 0; n < 3; ++n) {
-            w_m2[n] = w_m1[n];
-            w_m1[n] = w[n];
+            float up, dn;
+            syn_shares(u[3 * n], u[3 * n + 1], u[3 * n + 2], up, midn[n], dn);
+            s_up[buf][w][n][lane] = up;
+            s_dn[buf][w][n][lane] = dn;
         }
         __syncthreads();
+        if (out_row) {
+            float wv[3];
+#pragma unroll
+            for (int n = 0; n < 3; ++n) wv[n] = s_up[buf][w - 1][n][lane] + midn[n] + s_dn[buf][w + 1][n][lane];
+            // axis 2 (planes): plane cp - 1 from planes cp - 2, cp - 1, cp
+            if (cp >= c_begin + 1 && out_lane) {
+                float o = syn3(w_m2[0], w_m1[0], wv[0], w_m2[1], wv[1], w_m2[2], w_m1[2], wv[2]);
+                if (positivity && o < 0.0f) o = 0.0f;
+                f[(size_t)(cp - 1) * plane + (size_t)pb * n0 + pa] = o;
+            }
+#pragma unroll
+            for (int n = 0; n < 3; ++n) {
+                w_m2[n] = w_m1[n];
+                w_m1[n] = wv[n];
+            }
+        }
     }
 }
 
@@ -232,26 +271,18 @@ cbct_status launch_tf_analyze(int n0, int n1, int n2, const float *f, void *alph
     return check_cuda(cudaGetLastError(), "tf_analyze launch");
 }
 
-template <typename TA_T> static std::atomic<unsigned long long> g_synth_optin{0};
-
-template <typename TA_T> static cbct_status synth_optin()
-{
-    cudaError_t e = smem_optin_once(k_tf_synth_shrink<TA_T>, (int)TF_SYN_SMEM, g_synth_optin<TA_T>);
-    return e == cudaSuccess ? CBCT_OK : check_cuda(e, "tf_synth_shrink attribute");
-}
-
 template <typename TA_T>
 static cbct_status launch_tf_synth_shrink_t(int n0, int n1, int n2, const TA_T *alpha, float mu, int positivity,
                                             float *f, cudaStream_t st)
 {
-    {
-        cbct_status a = synth_optin<TA_T>();
-        if (a != CBCT_OK) return a;
-    }
-    const int chunk = tf_chunk(n0, n1, n2);
-    dim3 grid((n0 + TA - 1) / TA, (n1 + TB - 1) / TB, (n2 + chunk - 1) / chunk);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tf_synth_shrink<TA_T>, SY_THREADS, 0);
+    if (e != cudaSuccess) return check_cuda(e, "tf_synth_shrink occupancy");
+    const long long tiles = (long long)((n0 + SY_OUT - 1) / SY_OUT) * ((n1 + SY_ROWS - 1) / SY_ROWS);
+    const int chunk = fused_chunk(tiles, n2, (per_sm > 0 ? per_sm : 1) * device_sm_count());
+    dim3 grid((n0 + SY_OUT - 1) / SY_OUT, (n1 + SY_ROWS - 1) / SY_ROWS, (n2 + chunk - 1) / chunk);
     CBCT_TIMED(CBCT_KERNEL_TF_SYNTH, st,
-               k_tf_synth_shrink<TA_T><<<grid, dim3(TA, TB), TF_SYN_SMEM, st>>>(n0, n1, n2, chunk, alpha, mu, positivity, f));
+               k_tf_synth_shrink<TA_T><<<grid, dim3(32, SY_WARPS), 0, st>>>(n0, n1, n2, chunk, alpha, mu, positivity, f));
     return check_cuda(cudaGetLastError(), "tf_synth_shrink launch");
 }
 
@@ -420,35 +451,10 @@ template <int TAF> static cbct_status fused_optin()
 
 cbct_status tf_prepare()
 {
-    cbct_status r = synth_optin<float>();
-    if (r == CBCT_OK) r = synth_optin<__nv_bfloat16>();
-    if (r == CBCT_OK) r = synth_optin<__half>();
-    if (r == CBCT_OK) r = fused_optin<24>();
+    cbct_status r = fused_optin<24>();
     if (r == CBCT_OK) r = fused_optin<32>();
     if (r == CBCT_OK) r = fused_optin<36>();
     return r;
-}
-
-// Planes per block along axis 2 for the fused step: the split whose blocks fill whole
-// waves of the resident slots best, counting the two extra planes each block recomputes
-// at its start (a block's cost grows with chunk + 2).
-static int fused_chunk(long long tiles, int n2, int slots)
-{
-    int best = n2;
-    double best_eff = -1.0;
-    for (int nch = 1; nch <= n2; ++nch) {
-        const int chunk = (n2 + nch - 1) / nch;
-        if (nch > 1 && chunk == (n2 + nch - 2) / (nch - 1)) continue; // same split as nch - 1
-        const long long nb = tiles * ((n2 + chunk - 1) / chunk);
-        const long long waves = (nb + slots - 1) / slots;
-        const double eff = (double)n2 / ((double)((n2 + chunk - 1) / chunk) * (chunk + 2)) * (double)nb /
-                           ((double)waves * slots);
-        if (eff > best_eff + 1e-9) {
-            best_eff = eff;
-            best = chunk;
-        }
-    }
-    return best;
 }
 
 template <int TAF>

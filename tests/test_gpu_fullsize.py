@@ -163,3 +163,25 @@ def test_paper_scale_frame_round_trip(cb):
     f = dev(synth.random_volume(geom, 842, 0.0, 0.04))
     back = cb.tf_synthesize_shrink(cb.tf_analyze(f), 0.0, False)
     assert (torch.linalg.norm(back - f) / torch.linalg.norm(f)).item() <= 1e-6
+
+
+def test_paper_scale_shrink_synthesis_sampled(cb):
+    """The public shrink + synthesis H(W^T T_mu alpha) at 512x512x70 with mu > 0 and H on,
+    FP32 and BF16 coefficients, at 1000 voxels evaluated one by one by the oracle (from the
+    volume whose analysis alpha is). Bars: relative L2 over the samples 1e-5 (FP32) and
+    1e-3 (BF16: one rounding of each coefficient, relative 2^-9, averaged over 27 x 27
+    terms), measured before H, which is 1-Lipschitz."""
+    geom = synth.config_paper(40)
+    f = synth.voxelize(geom, synth.torso_ellipsoids(geom, 1002))
+    f = f + synth.random_volume(geom, 843, -0.002, 0.002)  # noise: many coefficients near mu
+    mu = 5e-4
+    sel = np.random.default_rng(844).choice(f.size, 1000, replace=False)
+    ref = oracle.tf_shrink_voxels(f, mu, True, sel)
+    pre = oracle.tf_shrink_voxels(f, mu, False, sel)
+    for dt, bar in ((torch.float32, 1e-5), (torch.bfloat16, 1e-3)):
+        alpha = cb.tf_analyze(dev(f), dtype=dt)
+        got = cb.tf_synthesize_shrink(alpha, mu, True).cpu().numpy().ravel()[sel]
+        del alpha
+        e = np.linalg.norm(got - ref) / np.linalg.norm(pre)
+        print(f"\nshrink + synthesis 512x512x70, {dt}: relative L2 over samples {e:.2e}")
+        assert e <= bar, (dt, e)

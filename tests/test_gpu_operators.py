@@ -187,7 +187,7 @@ def test_count_nnz_levels(cb):
             assert abs(n_gpu - n_ref) <= 5e-3 * n_ref, (lev, n_gpu, n_ref)
 
 
-TF_SHAPES = [(16, 64, 64), (5, 6, 7), (1, 4, 3), (2, 3, 5), (9, 17, 33), (3, 70, 40)]
+TF_SHAPES = [(16, 64, 64), (5, 6, 7), (1, 4, 3), (2, 3, 5), (9, 17, 33), (3, 70, 40), (4, 19, 61)]
 
 
 @pytest.mark.parametrize("shape", TF_SHAPES)
@@ -232,6 +232,24 @@ def test_tf_shrink_fused_parity(cb, shape, positive):
     # stays meaningful when H zeroes most voxels of a tiny random volume
     scale = np.linalg.norm(oracle.tf_synthesize_shrink(alpha, mu, False))
     assert np.linalg.norm(out - ref) <= 1e-5 * scale, np.linalg.norm(out - ref) / scale
+
+
+@pytest.mark.parametrize("layout", ["x_fastest", "z_fastest"])
+def test_tf_shrink_on_nonnegative_phantom(cb, layout):
+    """On a reconstruction-like volume (the seeded ellipsoid phantom, mu = 5e-4, H on) H
+    zeroes few voxels, so the plain relative-L2 bar of the frame transforms applies to the
+    fused step and to the public shrink + synthesis alike."""
+    geom = synth.config_small()
+    f = synth.voxelize(geom, synth.random_ellipsoids(geom, 1001))
+    if layout == "z_fastest":
+        f = np.ascontiguousarray(f.transpose(1, 2, 0))
+    mu = 5e-4
+    alpha = oracle.tf_analyze(f)
+    ref = oracle.tf_synthesize_shrink(alpha, mu, True)
+    out = cb.tf_shrink(dev(f), mu, True).cpu().numpy()
+    assert rel(out, ref) <= 1e-5, rel(out, ref)
+    out2 = cb.tf_synthesize_shrink(dev(alpha), mu, True).cpu().numpy()
+    assert rel(out2, ref) <= 1e-5, rel(out2, ref)
 
 
 def test_tf_round_trip_identity(cb):
