@@ -12,7 +12,9 @@
 // and so has weight (tb - ta): those rows form a contiguous range and are summed at once
 // from per-column prefix sums over rows (k_row_prefix); only the rows whose ray crosses
 // a z plane inside the column (about 0.1 per plane at the paper's sizes) are evaluated
-// one by one. The factor |D - S| is folded into the prefix sums. Every crossing parameter
+// one by one. The factor |D - S| is folded into the table, which holds for every row m
+// the pair (prefix of the rows below m, value of row m): one 8-byte load per plane gives
+// both the window's prefix and its straddling row. Every crossing parameter
 // uses the same helper expressions as the projector, so both operators use the same
 // FP32 weights. No atomics: the result is independent of scheduling. Lanes of a warp are
 // adjacent x voxels, which read adjacent imager columns.
@@ -64,23 +66,13 @@ __device__ __forceinline__ void straddle_rows(const GeomDev &G, float zp, float 
     hi = (int)floorf(fhi);
 }
 
-// Rows reaching plane zp inside the column lie in the window [a, b) of imager rows (at
-// most one row when the caller's `simple` test holds); a and b are clamped to [0, nv] so
-// that the prefixes col[a * nu], col[b * nu] exist (the table is [view][row][column]).
-// Returns those prefixes and the straddling row's weighted contributions below and above
-// the plane (zero if the window is empty).
-__device__ __forceinline__ void plane_terms(const GeomDev &G, const float *s_invv, const float2 *col, float zp,
-                                            float A, float B, float ta, float tb, float c0, float c1,
-                                            float2 &Pa, float2 &Pb, float &below, float &above)
+// The straddling row of a plane window [a, b) (b <= a + 1; table entry T = (P[a], g[a]))
+// split at the plane: its weighted value g (0 if the window is empty) times the part of
+// [ta, tb] below and above the plane z = zp.
+__device__ __forceinline__ void plane_split(const GeomDev &G, const float *s_invv, float2 T, int a, int b, float zp,
+                                            float ta, float tb, float &g, float &below, float &above)
 {
-    const float v0 = zp * A, v1 = zp * B;
-    const float nvf = (float)G.nv;
-    const float fa = fminf(fmaxf(fmaf(fminf(v0, v1), G.inv_dv, c0), 0.0f), nvf);
-    const float fb = fminf(fmaxf(fmaf(fmaxf(v0, v1), G.inv_dv, c1), -1.0f), nvf - 1.0f);
-    const int a = ceil_small(fa), b = floor_small(fb) + 1;
-    Pa = __ldg(col + a * G.nu); // (nv + 1) * nu < 2^31: 32-bit offsets
-    Pb = __ldg(col + max(a, b) * G.nu);
-    const float g = (Pb.x - Pa.x) + (Pb.y - Pa.y);
+    g = b > a ? T.y : 0.0f;
     const float iw = s_invv[min(a, G.nv - 1)];
     const float scl = fminf(fmaxf(tau_zplane(zp, iw, G.tc), ta), tb);
     const float wlo = scl - ta, whi = tb - scl;
@@ -89,25 +81,18 @@ __device__ __forceinline__ void plane_terms(const GeomDev &G, const float *s_inv
     above = g * (up ? whi : wlo);
 }
 
-// plane_terms for a window known to lie on the imager (0 <= fa, fb <= nv - 1 for every
-// plane of the chunk, checked by the caller at the extreme planes: both bounds grow with
-// the plane height). zs = zp / dv; (lo_f, hi_f) = (B, A) above z = 0 and (A, B) below, so
-// the window's lower and upper row bounds are zs * lo_f and zs * hi_f.
-__device__ __forceinline__ void plane_terms_inside(const GeomDev &G, const float *s_invv, const float2 *col,
-                                                   float zp, float zs, float lo_f, float hi_f, float ta, float tb,
-                                                   float c0, float c1, float2 &Pa, float2 &Pb, float &below,
-                                                   float &above)
+// Rows reaching plane zp inside the column lie in the window [a, b) of imager rows (at
+// most one row when the caller's `simple` test holds); a and b are clamped to [0, nv] so
+// that the table entry col[a * nu] exists (the table is [view][row 0..nv][column]).
+__device__ __forceinline__ void plane_window(const GeomDev &G, float zp, float A, float B, float c0, float c1,
+                                             int &a, int &b)
 {
-    const int a = ceil_small(fmaf(zs, lo_f, c0)), b = floor_small(fmaf(zs, hi_f, c1)) + 1;
-    Pa = __ldg(col + a * G.nu);
-    Pb = __ldg(col + max(a, b) * G.nu);
-    const float g = (Pb.x - Pa.x) + (Pb.y - Pa.y);
-    const float iw = s_invv[min(a, G.nv - 1)];
-    const float scl = fminf(fmaxf(tau_zplane(zp, iw, G.tc), ta), tb);
-    const float wlo = scl - ta, whi = tb - scl;
-    const bool up = iw > 0.0f; // z grows along the ray (v >= 0)
-    below = g * (up ? wlo : whi);
-    above = g * (up ? whi : wlo);
+    const float v0 = zp * A, v1 = zp * B;
+    const float nvf = (float)G.nv;
+    const float fa = fminf(fmaxf(fmaf(fminf(v0, v1), G.inv_dv, c0), 0.0f), nvf);
+    const float fb = fminf(fmaxf(fmaf(fmaxf(v0, v1), G.inv_dv, c1), -1.0f), nvf - 1.0f);
+    a = ceil_small(fa);
+    b = floor_small(fb) + 1;
 }
 
 // Register budget of the 8-voxel chunks: 9 resident blocks of 128 threads (56 registers, no
@@ -192,39 +177,48 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
                 const float fa_lo = fmaf(zs[0], zs[0] >= 0.0f ? B : A, c0);
                 const float fb_hi = fmaf(zs_top, zs_top >= 0.0f ? A : B, c1);
                 if (simple && fa_lo >= 0.0f && fb_hi <= (float)(G.nv - 1)) {
-                    // every window lies on the imager: no clamping
-                    float2 Pa, Pb;
-                    float below, above;
-                    plane_terms_inside(G, s_invv, col, zp[0], zs[0], zs[0] >= 0.0f ? B : A, zs[0] >= 0.0f ? A : B,
-                                       ta, tb, c0, c1, Pa, Pb, below, above);
+                    // every window lies on the imager: no clamping. Slab z receives the rows
+                    // strictly between the windows of planes z and z + 1 at weight tb - ta,
+                    // P[a_{z+1}] - P[a_z] - g_z, plus the split parts of both windows' rows.
+                    int a = ceil_small(fmaf(zs[0], zs[0] >= 0.0f ? B : A, c0));
+                    int b = floor_small(fmaf(zs[0], zs[0] >= 0.0f ? A : B, c1)) + 1;
+                    float2 T = __ldg(col + a * G.nu); // (nv + 1) * nu < 2^31: 32-bit offsets
+                    float g, below, above;
+                    plane_split(G, s_invv, T, a, b, zp[0], ta, tb, g, below, above);
                     acc[0] += above;
-                    float2 Pprev = Pb;
+                    float Pprev = T.x, gprev = g;
 #pragma unroll
                     for (int z = 0; z < ZC; ++z) {
                         if (z >= nzc) break;
                         const bool pos = zs[z + 1] >= 0.0f;
-                        plane_terms_inside(G, s_invv, col, zp[z + 1], zs[z + 1], pos ? B : A, pos ? A : B, ta, tb,
-                                           c0, c1, Pa, Pb, below, above);
-                        acc[z] = fmaf(wfull, (Pa.x - Pprev.x) + (Pa.y - Pprev.y), acc[z]) + below;
+                        a = ceil_small(fmaf(zs[z + 1], pos ? B : A, c0));
+                        b = floor_small(fmaf(zs[z + 1], pos ? A : B, c1)) + 1;
+                        T = __ldg(col + a * G.nu);
+                        plane_split(G, s_invv, T, a, b, zp[z + 1], ta, tb, g, below, above);
+                        acc[z] = fmaf(wfull, (T.x - Pprev) - gprev, acc[z]) + below;
                         if (z + 1 < ZC && z + 1 < nzc) acc[z + 1] += above;
-                        Pprev = Pb;
+                        Pprev = T.x;
+                        gprev = g;
                     }
                 } else if (simple) {
-                    // rows strictly between two planes' windows stay in the slab across the
-                    // column (weight tb - ta) and are summed as a prefix difference; the one
-                    // row in a plane's window is split at the plane
-                    float2 Pa, Pb;
-                    float below, above;
-                    plane_terms(G, s_invv, col, zp[0], A, B, ta, tb, c0, c1, Pa, Pb, below, above);
+                    // windows may leave the imager: clamped to [0, nv]
+                    int a, b;
+                    plane_window(G, zp[0], A, B, c0, c1, a, b);
+                    float2 T = __ldg(col + a * G.nu);
+                    float g, below, above;
+                    plane_split(G, s_invv, T, a, b, zp[0], ta, tb, g, below, above);
                     acc[0] += above;
-                    float2 Pprev = Pb;
+                    float Pprev = T.x, gprev = g;
 #pragma unroll
                     for (int z = 0; z < ZC; ++z) {
                         if (z >= nzc) break;
-                        plane_terms(G, s_invv, col, zp[z + 1], A, B, ta, tb, c0, c1, Pa, Pb, below, above);
-                        acc[z] = fmaf(wfull, (Pa.x - Pprev.x) + (Pa.y - Pprev.y), acc[z]) + below;
+                        plane_window(G, zp[z + 1], A, B, c0, c1, a, b);
+                        T = __ldg(col + a * G.nu);
+                        plane_split(G, s_invv, T, a, b, zp[z + 1], ta, tb, g, below, above);
+                        acc[z] = fmaf(wfull, (T.x - Pprev) - gprev, acc[z]) + below;
                         if (z + 1 < ZC && z + 1 < nzc) acc[z + 1] += above;
-                        Pprev = Pb;
+                        Pprev = T.x;
+                        gprev = g;
                     }
                 } else {
                     int lo_p, hi_p;
@@ -237,8 +231,8 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
                         float a = acc[z];
                         const int f0 = max(hi_p + 1, 0), f1 = min(lo_n - 1, G.nv - 1);
                         if (f0 <= f1) {
-                            const float2 P1 = __ldg(col + (f1 + 1) * G.nu), P0 = __ldg(col + f0 * G.nu);
-                            a = fmaf(wfull, (P1.x - P0.x) + (P1.y - P0.y), a);
+                            const float P1 = __ldg(col + (f1 + 1) * G.nu).x, P0 = __ldg(col + f0 * G.nu).x;
+                            a = fmaf(wfull, P1 - P0, a);
                         }
                         // rows that cross a z plane inside the column: exact overlap
                         const int r0 = max(lo_p, 0), r1 = min(hi_n, G.nv - 1);
@@ -250,10 +244,7 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
                             const float iw = s_invv[iv];
                             const float s0 = tau_zplane(zp[z], iw, G.tc), s1 = tau_zplane(zp[z + 1], iw, G.tc);
                             const float lo = fmaxf(ta, fminf(s0, s1)), hi = fminf(tb, fmaxf(s0, s1));
-                            if (hi > lo) {
-                                const float2 Q1 = __ldg(col + (iv + 1) * G.nu), Q0 = __ldg(col + iv * G.nu);
-                                a = fmaf((Q1.x - Q0.x) + (Q1.y - Q0.y), hi - lo, a);
-                            }
+                            if (hi > lo) a = fmaf(__ldg(col + iv * G.nu).y, hi - lo, a);
                         }
                         acc[z] = a;
                         lo_p = lo_n;
@@ -337,17 +328,18 @@ cbct_status launch_backproject(const GeomDev &G, const float2 *ps, float *out, l
 
 // Prefix sums over imager rows of every (view k, imager column iu), stored row-major like
 // the projections so that neighbouring lanes (columns) touch neighbouring addresses:
-// ps[k][m][iu] = sum_{iv < m} w(iv) g[k][iv][iu], m = 0..nv, with w = |D - S| if
-// `prescale` (folds the ray length into the adjoint's input) and 1 otherwise. Sums are
-// kept as a compensated float pair (sum, correction), so differences of two prefixes keep
-// FP32 relative accuracy however long the column. A block covers 32
-// columns (lanes, coalesced reads) of one view; its 16 warps take consecutive row chunks:
-// pass 1 sums each chunk, the chunk offsets come from shared memory, pass 2 writes.
+// ps[k][m][iu] = (P_m, w(m) g[k][m][iu]) for m = 0..nv, where P_m = sum_{iv < m} w(iv)
+// g[k][iv][iu] and the second member is row m's own weighted value (0 at m = nv), with
+// w = |D - S| if `prescale` (folds the ray length into the adjoint's input) and 1
+// otherwise. The running sums are compensated (Neumaier) and rounded to FP32 once per
+// entry, so a difference of two prefixes carries at most two roundings of the prefixes'
+// magnitude. A block covers 32 columns (lanes, coalesced reads) of one view; its 16 warps
+// take consecutive row chunks: pass 1 sums each chunk, the chunk offsets come from shared
+// memory, pass 2 writes.
 constexpr int PREFIX_WARPS = 16;
 
 // Compensated FP32 summation (Neumaier): s + c carries the running sum to about twice
-// FP32's precision, so the stored pair (s, c) differences keep FP32 relative accuracy even
-// for short row ranges of a long column. (FP64 arithmetic is much slower on this part.)
+// FP32's precision. (FP64 arithmetic is much slower on this part.)
 __device__ __forceinline__ void comp_add(float &s, float &c, float v)
 {
     const float t = s + v;
@@ -389,14 +381,14 @@ k_row_prefix(GeomDev G, const T *__restrict__ g, float2 *__restrict__ ps, int pr
         rc += t.y;
     }
     if (!ok) return;
-    float2 *dst = ps + (size_t)k * ((size_t)G.nv + 1) * G.nu + iu; // prefix m at dst[m * nu]
-    if (w == 0) dst[0] = make_float2(0.0f, 0.0f);
+    float2 *dst = ps + (size_t)k * ((size_t)G.nv + 1) * G.nu + iu; // entry m at dst[m * nu]
     for (int iv = r0; iv < r1; ++iv) {
         float val = load_as_float(src + (size_t)iv * G.nu);
         if (prescale) val *= ray_length(dxr, dyr, imager_v(G, iv));
+        dst[(size_t)iv * G.nu] = make_float2(rs + rc, val);
         comp_add(rs, rc, val);
-        dst[(size_t)(iv + 1) * G.nu] = make_float2(rs, rc);
     }
+    if (w == PREFIX_WARPS - 1) dst[(size_t)G.nv * G.nu] = make_float2(rs + rc, 0.0f); // all rows
 }
 
 cbct_status launch_row_prefix(const GeomDev &G, const void *g, float2 *ps, int prescale, cudaStream_t st, int storage)

@@ -196,7 +196,8 @@ cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long 
                            int storage = ST_F32, const Scalars *sc = nullptr);
 int backproject_num_blocks(const GeomDev &G);
 // ps: per-(view, imager column) prefix sums over rows of the |D - S|-weighted stack,
-// [n_views][nv + 1][nu] float2 (hi, lo), built by launch_row_prefix.
+// [n_views][nv + 1][nu] float2 (prefix of the rows below m, value of row m), built by
+// launch_row_prefix.
 cbct_status launch_backproject(const GeomDev &G, const float2 *ps, float *out, long long sx,
                                long long sy, long long sz, float *out2, double *partials,
                                cudaStream_t st);
