@@ -16,13 +16,24 @@
 // the pair (prefix of the rows below m, value of row m): one 8-byte load per plane gives
 // both the window's prefix and its straddling row. Every crossing parameter
 // uses the same helper expressions as the projector, so both operators use the same
-// FP32 weights. No atomics: the result is independent of scheduling. Lanes of a warp are
-// adjacent x voxels, which read adjacent imager columns.
+// FP32 weights. No atomics: the result is independent of scheduling.
 #include "cbct_internal.cuh"
 
 namespace cbct {
 
-constexpr int BP_TX = 32, BP_TY = 4;
+// Thread mapping: a block of 128 threads owns a BP_BX x BP_BY tile of voxel columns; each
+// warp takes a BP_WX x (32 / BP_WX) patch of it. Lanes whose columns are close in both x
+// and y read nearby table entries in every view (a voxel's imager column moves with x at
+// some views and with y at others): an 8 x 4 patch touches 4.5 sectors per table request
+// where a 32 x 1 row touches 15.9, and the four warps of a block share their lines in L1.
+#ifndef CBCT_BP_WX
+#define CBCT_BP_WX 8
+#endif
+constexpr int BP_THREADS = 128;
+constexpr int BP_WX = CBCT_BP_WX, BP_WY = 32 / BP_WX;     // warp patch
+constexpr int BP_WPX = BP_WX == 8 ? 2 : 1, BP_WPY = 4 / BP_WPX; // warps per block along x, y
+constexpr int BP_BX = BP_WX * BP_WPX, BP_BY = BP_WY * BP_WPY;  // block tile
+static_assert(BP_WX * BP_WY == 32 && BP_WPX * BP_WPY * 32 == BP_THREADS, "block tiling");
 
 // resident blocks per SM the register budget of the 16-voxel chunks is sized for (64
 // registers, no spills)
@@ -38,7 +49,7 @@ constexpr int BP_TX = 32, BP_TY = 4;
 // fewer than 4 blocks per SM.
 static int bp_zchunk(const GeomDev &G)
 {
-    const long long tiles = (long long)((G.nx + BP_TX - 1) / BP_TX) * ((G.ny + BP_TY - 1) / BP_TY);
+    const long long tiles = (long long)((G.nx + BP_BX - 1) / BP_BX) * ((G.ny + BP_BY - 1) / BP_BY);
     const long long sms = device_sm_count();
     if (tiles * ((G.nz + 15) / 16) >= 6LL * CBCT_BP_Z16_BLOCKS * sms) return 16;
     const long long want = 4LL * sms;
@@ -47,10 +58,15 @@ static int bp_zchunk(const GeomDev &G)
     return zc;
 }
 
+int backproject_max_blocks(const GeomDev &G)
+{
+    return ((G.nx + BP_BX - 1) / BP_BX) * ((G.ny + BP_BY - 1) / BP_BY) * G.nz; // one z voxel per thread
+}
+
 int backproject_num_blocks(const GeomDev &G)
 {
     const int zc = bp_zchunk(G);
-    return ((G.nx + BP_TX - 1) / BP_TX) * ((G.ny + BP_TY - 1) / BP_TY) * ((G.nz + zc - 1) / zc);
+    return ((G.nx + BP_BX - 1) / BP_BX) * ((G.ny + BP_BY - 1) / BP_BY) * ((G.nz + zc - 1) / zc);
 }
 
 // Rows whose ray, while inside the column (tau in [ta, tb], 1/(tc+ta) = A, 1/(tc+tb) = B),
@@ -103,21 +119,21 @@ __device__ __forceinline__ void plane_window(const GeomDev &G, float zp, float A
 #define CBCT_BP_MIN_BLOCKS 9
 #endif
 template <int ZC, bool FLAT>
-__global__ void __launch_bounds__(BP_TX *BP_TY, ZC >= 16 ? CBCT_BP_Z16_BLOCKS : ZC >= 8 ? CBCT_BP_MIN_BLOCKS : 1)
+__global__ void __launch_bounds__(BP_THREADS, ZC >= 16 ? CBCT_BP_Z16_BLOCKS : ZC >= 8 ? CBCT_BP_MIN_BLOCKS : 1)
 k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out, int sx, int sy, int sz,
               float *__restrict__ out2, double *__restrict__ partials)
 {
     extern __shared__ float s_invv[]; // 1 / v per imager row
-    __shared__ double s_warp[BP_TX * BP_TY / 32];
-    const int tid = threadIdx.y * BP_TX + threadIdx.x;
-    for (int i = tid; i < G.nv; i += BP_TX * BP_TY) {
+    __shared__ double s_warp[BP_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < G.nv; i += BP_THREADS) {
         const float v = imager_v(G, i);
         s_invv[i] = v != 0.0f ? __frcp_rn(v) : 1e30f;
     }
     __syncthreads();
 
-    const int ix = blockIdx.x * BP_TX + threadIdx.x;
-    const int iy = blockIdx.y * BP_TY + threadIdx.y;
+    const int ix = blockIdx.x * BP_BX + (warp % BP_WPX) * BP_WX + lane % BP_WX;
+    const int iy = blockIdx.y * BP_BY + (warp / BP_WPX) * BP_WY + lane / BP_WX;
     const int iz0 = blockIdx.z * ZC;
     const bool ok = ix < G.nx && iy < G.ny;
     float acc[ZC];
@@ -292,7 +308,7 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
         __syncthreads();
         if (tid == 0) {
             double t = 0.0;
-            for (int w = 0; w < BP_TX * BP_TY / 32; ++w) t += s_warp[w];
+            for (int w = 0; w < BP_THREADS / 32; ++w) t += s_warp[w];
             partials[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
         }
     }
@@ -302,8 +318,8 @@ cbct_status launch_backproject(const GeomDev &G, const float2 *ps, float *out, l
                                long long sz, float *out2, double *partials, cudaStream_t st)
 {
     const int zc = bp_zchunk(G);
-    dim3 block(BP_TX, BP_TY);
-    dim3 grid((G.nx + BP_TX - 1) / BP_TX, (G.ny + BP_TY - 1) / BP_TY, (G.nz + zc - 1) / zc);
+    dim3 block(BP_THREADS);
+    dim3 grid((G.nx + BP_BX - 1) / BP_BX, (G.ny + BP_BY - 1) / BP_BY, (G.nz + zc - 1) / zc);
     const size_t smem = sizeof(float) * G.nv;
     const int isx = (int)sx, isy = (int)sy, isz = (int)sz;
     ProfToken tok = prof_start(CBCT_KERNEL_BACKPROJECT, st);

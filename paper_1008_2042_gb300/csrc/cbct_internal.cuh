@@ -195,6 +195,8 @@ cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long 
                            double *partials, float count_thr, cudaStream_t st,
                            int storage = ST_F32, const Scalars *sc = nullptr);
 int backproject_num_blocks(const GeomDev &G);
+// Upper bound of backproject_num_blocks over every grid no larger than G's (any z chunk).
+int backproject_max_blocks(const GeomDev &G);
 // ps: per-(view, imager column) prefix sums over rows of the |D - S|-weighted stack,
 // [n_views][nv + 1][nu] float2 (prefix of the rows below m, value of row m), built by
 // launch_row_prefix.

@@ -345,8 +345,8 @@ static size_t max_partials(const cbct_geometry *g)
 {
     GeomDev G = level_geom(g, 0);
     size_t a = (size_t)project_num_blocks(G);
-    // backprojection blocks are largest with one z voxel per thread at the finest grid
-    size_t b = (size_t)((G.nx + 31) / 32) * ((G.ny + 3) / 4) * G.nz;
+    // backprojection blocks are most numerous with one z voxel per thread at the finest grid
+    size_t b = (size_t)backproject_max_blocks(G);
     return a > b ? a : b;
 }
 
