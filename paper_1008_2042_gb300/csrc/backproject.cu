@@ -19,6 +19,8 @@
 // FP32 weights. No atomics: the result is independent of scheduling.
 #include "cbct_internal.cuh"
 
+#include <type_traits>
+
 namespace cbct {
 
 // Thread mapping: a block of 128 threads owns a BP_BX x BP_BY tile of voxel columns; each
@@ -93,6 +95,19 @@ __device__ __forceinline__ void plane_split(const GeomDev &G, const float *s_inv
     const float scl = fminf(fmaxf(tau_zplane(zp, iw, G.tc), ta), tb);
     const float wlo = scl - ta, whi = tb - scl;
     const bool up = iw > 0.0f; // z grows along the ray (v >= 0)
+    below = g * (up ? wlo : whi);
+    above = g * (up ? whi : wlo);
+}
+
+// plane_split for a window on the imager (a <= nv - 1: the row exists).
+__device__ __forceinline__ void plane_split_inside(const float *s_invv, float tc, float2 T, int a, int b, float zp,
+                                                   float ta, float tb, float &g, float &below, float &above)
+{
+    g = b > a ? T.y : 0.0f;
+    const float iw = s_invv[a];
+    const float scl = fminf(fmaxf(tau_zplane(zp, iw, tc), ta), tb);
+    const float wlo = scl - ta, whi = tb - scl;
+    const bool up = iw > 0.0f;
     below = g * (up ? wlo : whi);
     above = g * (up ? whi : wlo);
 }
@@ -196,26 +211,42 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
                     // every window lies on the imager: no clamping. Slab z receives the rows
                     // strictly between the windows of planes z and z + 1 at weight tb - ta,
                     // P[a_{z+1}] - P[a_z] - g_z, plus the split parts of both windows' rows.
-                    int a = ceil_small(fmaf(zs[0], zs[0] >= 0.0f ? B : A, c0));
-                    int b = floor_small(fmaf(zs[0], zs[0] >= 0.0f ? A : B, c1)) + 1;
-                    float2 T = __ldg(col + a * G.nu); // (nv + 1) * nu < 2^31: 32-bit offsets
-                    float g, below, above;
-                    plane_split(G, s_invv, T, a, b, zp[0], ta, tb, g, below, above);
-                    acc[0] += above;
-                    float Pprev = T.x, gprev = g;
+                    // The window of plane zp spans rows v in [zp B, zp A] above z = 0 and
+                    // [zp A, zp B] below; a chunk whose planes all lie on one side (all but
+                    // one chunk of a column) fixes that choice for the whole visit.
+                    auto planes = [&](auto side) {
+                        constexpr int S = decltype(side)::value; // +1 / -1: every plane at z >= 0 / <= 0
+                        auto bounds = [&](float zsv, float &lo_f, float &hi_f) {
+                            const bool pos = S > 0 || (S == 0 && zsv >= 0.0f);
+                            lo_f = pos ? B : A;
+                            hi_f = pos ? A : B;
+                        };
+                        float lo_f, hi_f;
+                        bounds(zs[0], lo_f, hi_f);
+                        int a = ceil_small(fmaf(zs[0], lo_f, c0));
+                        int b = floor_small(fmaf(zs[0], hi_f, c1)) + 1;
+                        float2 T = __ldg(col + a * G.nu); // (nv + 1) * nu < 2^31: 32-bit offsets
+                        float g, below, above;
+                        plane_split_inside(s_invv, G.tc, T, a, b, zp[0], ta, tb, g, below, above);
+                        acc[0] += above;
+                        float Pprev = T.x, gprev = g;
 #pragma unroll
-                    for (int z = 0; z < ZC; ++z) {
-                        if (z >= nzc) break;
-                        const bool pos = zs[z + 1] >= 0.0f;
-                        a = ceil_small(fmaf(zs[z + 1], pos ? B : A, c0));
-                        b = floor_small(fmaf(zs[z + 1], pos ? A : B, c1)) + 1;
-                        T = __ldg(col + a * G.nu);
-                        plane_split(G, s_invv, T, a, b, zp[z + 1], ta, tb, g, below, above);
-                        acc[z] = fmaf(wfull, (T.x - Pprev) - gprev, acc[z]) + below;
-                        if (z + 1 < ZC && z + 1 < nzc) acc[z + 1] += above;
-                        Pprev = T.x;
-                        gprev = g;
-                    }
+                        for (int z = 0; z < ZC; ++z) {
+                            if (z >= nzc) break;
+                            bounds(zs[z + 1], lo_f, hi_f);
+                            a = ceil_small(fmaf(zs[z + 1], lo_f, c0));
+                            b = floor_small(fmaf(zs[z + 1], hi_f, c1)) + 1;
+                            T = __ldg(col + a * G.nu);
+                            plane_split_inside(s_invv, G.tc, T, a, b, zp[z + 1], ta, tb, g, below, above);
+                            acc[z] = fmaf(wfull, (T.x - Pprev) - gprev, acc[z]) + below;
+                            if (z + 1 < ZC) acc[z + 1] += above; // acc[nzc] is never stored
+                            Pprev = T.x;
+                            gprev = g;
+                        }
+                    };
+                    if (zs[0] >= 0.0f) planes(std::integral_constant<int, 1>());
+                    else if (zs_top <= 0.0f) planes(std::integral_constant<int, -1>());
+                    else planes(std::integral_constant<int, 0>());
                 } else if (simple) {
                     // windows may leave the imager: clamped to [0, nv]
                     int a, b;
