@@ -45,9 +45,9 @@ N_CGLS = 3
 LEVELS = 3
 TOTAL_ITERS = 50
 PHOTONS = 5e4
-# FP32 arithmetic operations counted per ray-voxel update (roofline numerator): next
-# plane-crossing parameter (FMA), nearest crossing (min), segment length (subtract),
-# accumulation (FMA).
+# FP32 arithmetic operations counted per ray-voxel update in the secondary arithmetic model
+# of the roofline: next plane-crossing parameter (FMA), nearest crossing (min), segment
+# length (subtract), accumulation (FMA).
 OPS_PER_UPDATE = 4
 FP32_LANES_PER_SM = 128
 
@@ -62,6 +62,8 @@ def parse_args(argv=None):
     ap.add_argument("--storage", default="f32", choices=("f32", "bf16", "f16"),
                     help="storage type of the CGLS residual and projected direction (arithmetic stays FP32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the extra measurements (frame transforms, 16-bit storage, 80 views)")
     ap.add_argument("--cpu-views", type=int, default=40,
                     help="views in the oracle's bounded sample (CPU baseline); the reference arm uses 16 per step")
     return ap.parse_args(argv)
@@ -186,31 +188,19 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def kernel_sources_sha(kernel: str) -> str:
-    """sha256 over the CUDA sources that define a kernel (its source files and the internal
-    header), to tie a stored ncu traffic figure to the kernel version it was taken on."""
-    import hashlib
-    csrc = os.path.join(ROOT, "paper_1008_2042_gb300", "csrc")
-    files = {"k_project": ("project.cu", "project.cuh", "project_kernel.cuh"),
-             "k_backproject": ("backproject.cu",)}[kernel]
-    h = hashlib.sha256()
-    for name in files + ("cbct_internal.cuh",):
-        with open(os.path.join(csrc, name), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()
-
-
-def stored_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None when the
-    kernel's sources changed since that capture (or there is none)."""
+def stored_counters(kernel: str):
+    """Per-level ncu counters of `kernel` (one launch per multigrid level, profiles/kernels.json,
+    written by paper_1008_2042_gb300.profile_counters), or None when the kernel's sources
+    changed since that capture (or there is none)."""
+    from paper_1008_2042_gb300.profile_counters import kernel_sources_sha
     try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+        with open(os.path.join(ROOT, "profiles", "kernels.json")) as fh:
             rec = json.load(fh).get(kernel)
     except (OSError, ValueError):
         return None
     if not rec or rec.get("sources_sha256") != kernel_sources_sha(kernel):
         return None
-    return rec.get("dram_bytes_per_launch")
+    return rec.get("levels")
 
 
 def measured_peaks():
@@ -322,6 +312,47 @@ def run_reference(args):
 # The CUDA path
 # ---------------------------------------------------------------------------------------
 
+def make_problem(cb, geom, dev, rank: int):
+    """The benchmark's input on `geom`: the seeded torso phantom (seed 1002), projected by
+    the library's P, with Poisson noise at PHOTONS per ray (seed 2002 + rank). The same
+    phantom and noise seed, projected by the oracle, are the input of the paper-scale
+    reconstruction parity test, which also checks the library's P of this phantom against
+    the oracle's over the whole stack."""
+    import torch
+    g = cb.Geometry(geom)
+    f_true = torch.tensor(synth.voxelize(geom, synth.torso_ellipsoids(geom, 1002)), dtype=torch.float32, device=dev)
+    p_ideal = cb.project(g, f_true).double().cpu().numpy()
+    y_host = torch.tensor(synth.noisy_line_integrals(p_ideal, PHOTONS, 2002 + rank), dtype=torch.float32).pin_memory()
+    nnz = [cb.count_nnz(g, lev) for lev in range(LEVELS)]  # level 0 = finest
+    return g, y_host, nnz
+
+
+def launches_per_level(iters):
+    """P and P^T launches a reconstruction makes on each level (level 0 = finest):
+    n_cgls + 1 P and n_cgls P^T per A2 iteration."""
+    return ([iters[LEVELS - 1 - lev] * (N_CGLS + 1) for lev in range(LEVELS)],
+            [iters[LEVELS - 1 - lev] * N_CGLS for lev in range(LEVELS)])
+
+
+def time_reconstructions(cb, g, y, iters, steps, flush, storage="f32", ws=None, out=None):
+    """Device seconds per reconstruction: mean of `steps` runs after one warm-up, each
+    bracketed by CUDA events on the launching stream, the L2 flushed before each."""
+    import torch
+    stream = torch.cuda.current_stream()
+    cb.reconstruct(g, y, MU, LEVELS, iters, n_cgls=N_CGLS, workspace=ws, out=out, storage=storage)
+    torch.cuda.synchronize()
+    total = 0.0
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cb.reconstruct(g, y, MU, LEVELS, iters, n_cgls=N_CGLS, workspace=ws, out=out, storage=storage)
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1) / 1e3
+    return total / steps
+
+
 def run_ours(args):
     import torch
 
@@ -334,16 +365,11 @@ def run_ours(args):
     import paper_1008_2042_gb300 as cb
 
     geom, iters = workload(args.views)
-    g = cb.Geometry(geom)
-    # input: seeded torso phantom, projected with the library's projector, Poisson noise
-    f_true = torch.tensor(synth.voxelize(geom, synth.torso_ellipsoids(geom, 1002)), dtype=torch.float32, device=dev)
-    p_ideal = cb.project(g, f_true).double().cpu().numpy()
-    y_host = torch.tensor(synth.noisy_line_integrals(p_ideal, PHOTONS, 2002 + rank), dtype=torch.float32).pin_memory()
+    g, y_host, nnz = make_problem(cb, geom, dev, rank)
     y = y_host.to(dev)
-    nnz = [cb.count_nnz(g, lev) for lev in range(LEVELS)]  # level 0 = finest
-    p_per_iter, pt_per_iter = N_CGLS + 1, N_CGLS
-    updates_P = sum(iters[LEVELS - 1 - lev] * p_per_iter * nnz[lev] for lev in range(LEVELS))
-    updates_PT = sum(iters[LEVELS - 1 - lev] * pt_per_iter * nnz[lev] for lev in range(LEVELS))
+    np_lev, npt_lev = launches_per_level(iters)
+    updates_P = sum(np_lev[lev] * nnz[lev] for lev in range(LEVELS))
+    updates_PT = sum(npt_lev[lev] * nnz[lev] for lev in range(LEVELS))
     updates = updates_P + updates_PT
 
     ws = torch.empty(cb.reconstruct_workspace_size(g), dtype=torch.uint8, device=dev)
@@ -396,58 +422,103 @@ def run_ours(args):
     secs, total_updates = aggregate(local_s, updates * args.steps, dist)
     value = total_updates / secs
 
-    # ---- end to end through the public API: host buffers, copies inside the timed region ----
+    # ---- end to end through the public API: host buffers, copies inside the timed region;
+    # the same L2 flush as above before every step, outside its event pair ----
     out_host = torch.empty(geom.vol_shape, dtype=torch.float32).pin_memory()
     y_dev = torch.empty_like(y)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ee[k][0].record(stream)
         y_dev.copy_(y_host, non_blocking=True)
         step(y_dev, out)
         out_host.copy_(out, non_blocking=True)
-    e1.record(stream)
+        ee[k][1].record(stream)
     torch.cuda.synchronize()
-    e2e_s, _ = aggregate(e0.elapsed_time(e1) / 1e3, 0.0, dist)
+    e2e_s, _ = aggregate(sum(a.elapsed_time(b) for a, b in ee) / 1e3, 0.0, dist)
     e2e_value = total_updates / e2e_s
 
     # ---- roofline of the dominant kernel (P or P^T), from the live event timings ----
     peaks = measured_peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
-    alu_peak = sms * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12  # T FP32 ops/s (one per lane per clock)
+    alu_peak = sms * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12  # T thread instructions/s (one per lane per clock)
     ms_p, n_p = ktimes["project"]
     ms_pt, n_pt = ktimes["backproject"]
     if ms_p >= ms_pt:
-        dom, kname, ms_dom, n_dom, upd_dom = "project (P, Siddon column sweep)", "k_project", ms_p, n_p, updates_P * args.steps
+        dom, kname, ms_dom, n_dom, upd_dom, per_lev = ("project (P, Siddon column sweep)", "k_project", ms_p, n_p,
+                                                       updates_P * args.steps, np_lev)
     else:
-        dom, kname, ms_dom, n_dom, upd_dom = "backproject (exact P^T gather)", "k_backproject", ms_pt, n_pt, updates_PT * args.steps
-    achieved = (upd_dom * OPS_PER_UPDATE / max(n_dom, 1)) / (ms_dom / max(n_dom, 1) / 1e3) / 1e12
+        dom, kname, ms_dom, n_dom, upd_dom, per_lev = ("backproject (exact P^T gather)", "k_backproject", ms_pt,
+                                                       n_pt, updates_PT * args.steps, npt_lev)
+    avg_s = ms_dom / max(n_dom, 1) / 1e3
+    counters = stored_counters(kname)
     roofline = {
-        "bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-        "frac": achieved / alu_peak, "traffic": stored_traffic(kname),
-        "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz (one FP32 op per lane "
-                       f"per clock; {OPS_PER_UPDATE} FP32 ops counted per ray-voxel update)",
-        "avg_launch_ms": ms_dom / max(n_dom, 1),
+        "bound": "alu", "kernel": dom, "unit": "T thread-instructions/s", "peak": alu_peak,
+        "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} lanes x {sm_max:.0f} MHz: one instruction per lane per clock "
+                       f"(no pipe, L1 or DRAM saturates: the kernel is issue- and latency-bound)",
+        "avg_launch_ms": avg_s * 1e3,
         "kernel_share": {k: round(v / sum(family_ms.values()), 4) for k, v in family_ms.items()}
         if sum(family_ms.values()) else {},
-        "hbm_compulsory_gbs": None,
     }
+    # secondary arithmetic model: OPS_PER_UPDATE FP32 operations per ray-voxel update
+    model = (upd_dom * OPS_PER_UPDATE / max(n_dom, 1)) / avg_s / 1e12
+    roofline["model_4ops_per_update"] = {"achieved": model, "frac": model / alu_peak}
+    if counters:
+        # instructions and DRAM bytes the step's launches execute, from one ncu launch per level
+        # weighted by the launches per level, over the live average launch time
+        w = [per_lev[lev] * args.steps for lev in range(LEVELS)]
+        tot = sum(w)
+        inst = sum(w[lev] * counters[str(lev)]["thread_inst"] for lev in range(LEVELS)) / tot
+        traffic = sum(w[lev] * (counters[str(lev)]["dram_read_bytes"] + counters[str(lev)]["dram_write_bytes"])
+                      for lev in range(LEVELS)) / tot
+        roofline.update({
+            "achieved": inst / avg_s / 1e12, "frac": inst / avg_s / 1e12 / alu_peak, "traffic": traffic,
+            "achieved_basis": "thread instructions per launch (ncu smsp__thread_inst_executed.sum, one launch per "
+                              "level, weighted by the step's launches per level) / live average launch duration",
+            "issue_active_ncu_pct": {lev: counters[lev]["issue_active_pct"] for lev in counters},
+            "l1_throughput_ncu_pct": {lev: counters[lev]["l1_throughput_pct"] for lev in counters},
+            "thread_inst_per_update": {str(lev): counters[str(lev)]["thread_inst"] / nnz[lev] for lev in range(LEVELS)},
+            "counters": "profiles/kernels.json",
+        })
+    else:
+        roofline.update({"achieved": model, "frac": model / alu_peak, "traffic": None,
+                         "achieved_basis": f"{OPS_PER_UPDATE} FP32 operations per ray-voxel update (no ncu counters "
+                                           f"for the current kernel sources)"})
     # compulsory DRAM bytes of P at the finest level: read the volume, write the stack
     n0 = geom.nx * geom.ny * geom.nz
     m0 = geom.n_views * geom.nv * geom.nu
-    roofline["hbm_compulsory_gbs"] = 4.0 * (n0 + m0) / (ms_dom / max(n_dom, 1) / 1e3) / 1e9
+    roofline["hbm_compulsory_gbs"] = 4.0 * (n0 + m0) / avg_s / 1e9
+
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra:
+        # the public frame transforms against HBM; the reconstruction with 16-bit CGLS vectors
+        # and at 80 views (the second view count of the workload)
+        extra["frame_transforms_hbm"] = time_frame_transforms(cb, geom, dev)
+        for st in ("bf16", "f16"):
+            if st != args.storage:
+                extra[f"recon_seconds_{st}_storage"] = time_reconstructions(cb, g, y, iters, 3, flush, st, ws, out)
+        if args.views == 40:
+            del ws
+            g80, y80_host, nnz80 = make_problem(cb, synth.config_paper(80), dev, rank)
+            ws80 = torch.empty(cb.reconstruct_workspace_size(g80), dtype=torch.uint8, device=dev)
+            t80 = time_reconstructions(cb, g80, y80_host.to(dev), iters, 3, flush, args.storage, ws80, out)
+            np80, npt80 = launches_per_level(iters)
+            u80 = sum((np80[lev] + npt80[lev]) * nnz80[lev] for lev in range(LEVELS))
+            extra["recon_80_views"] = {"seconds": t80, "updates_per_s": u80 / t80, "nnz_per_P": nnz80,
+                                       "storage": args.storage}
+            g80.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            u, s, cores = oracle_sample(geom, args.cpu_views, 3003)
-            cpu = {"value": u / s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            u, s_, cores = oracle_sample(geom, args.cpu_views, 3003)
+            cpu = {"value": u / s_, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": f"P + P^T of {args.cpu_views} of the {geom.n_views} views of the same workload "
-                             f"({s:.1f} s)"}
+                             f"({s_:.1f} s)"}
         except Exception as exc:  # the oracle is a reported baseline only
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {exc}"}
 
@@ -473,6 +544,7 @@ def run_ours(args):
             "family_ms_one_profiled_step": family_ms,
             "clocks": clocks,
         }
+        line.update(extra)
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
