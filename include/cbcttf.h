@@ -272,19 +272,22 @@ cbct_status cbct_count_nnz(const cbct_geometry *geom, int level, unsigned long l
                            cbct_stream_t stream);
 
 /*
- * Forward projection without device allocation. Same operation and result as
- * cbct_project, for callers that cannot allocate device memory while they run (for
- * example work enqueued during CUDA stream capture, or a service whose device memory is
- * fixed at start-up). The paper has no counterpart: this is an interface variant, not a
- * step of the method. Instead of the geometry's lazily allocated scratch it uses one
- * fixed scratch array of CBCT_PROJECT_STATIC_MAX_VOXELS floats that the library places
- * on every GPU that loads it, held until the process exits. Volumes larger than that are
- * rejected with CBCT_ERR_INVALID_ARG. The geometry must have been created beforehand.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture. All calls share the one array, so
- * calls whose work overlaps on the GPU (different streams, or several host threads)
- * race and must be serialised by the caller. Each call overwrites the part of the array
- * it uses before reading it, so no clearing is needed.
+ * Forward projection without device allocation. Same operation and result (bit for bit)
+ * as cbct_project, for callers that cannot allocate device memory while they run: a
+ * service that fixes its device memory footprint at start-up and treats any later
+ * allocation as a failure, or a latency-critical loop that cannot afford the device-wide
+ * synchronisation an allocation may cause. The paper has no counterpart: this is an
+ * interface variant, not a step of the method. Instead of the geometry's lazily
+ * allocated scratch it uses one fixed scratch array of CBCT_PROJECT_STATIC_MAX_VOXELS
+ * floats that the library places on every GPU that loads it, held until the process
+ * exits. Volumes larger than that are rejected with CBCT_ERR_INVALID_ARG. The geometry
+ * must have been created beforehand. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and keeps it for the life of the process; make
+ * that first call before any stream capture. A device reset (cudaDeviceReset) after the
+ * first call is not supported: the kept address would no longer be valid. All calls
+ * share the one array, so calls whose work overlaps on the GPU (different streams, or
+ * several host threads) race and must be serialised by the caller. Each call overwrites
+ * the part of the array it uses before reading it, so no clearing is needed.
  */
 #define CBCT_PROJECT_STATIC_MAX_VOXELS 4194304
 cbct_status cbct_project_static(const cbct_geometry *geom, const float *f, float *g,

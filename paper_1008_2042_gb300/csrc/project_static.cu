@@ -1,11 +1,11 @@
 // cbct_project_static: the forward projection of cbct_project for callers that must not
-// allocate device memory once they are running, e.g. code that enqueues work while a
-// CUDA stream is being captured into a graph (where cudaMalloc is not permitted), or
-// services that fix their device memory footprint at start-up and treat any later
-// allocation as a failure. cbct_project keeps its scratch (the volume rearranged into
-// the projector's z-contiguous layout) in memory it allocates on first use; this entry
-// point keeps the same scratch in a fixed array compiled into the library instead, so a
-// call allocates nothing.
+// allocate device memory once they are running, e.g. services that fix their device
+// memory footprint at start-up and treat any later allocation as a failure, or
+// latency-critical loops that cannot afford the device-wide synchronisation an allocation
+// may cause. cbct_project keeps its scratch (the volume rearranged into the projector's
+// z-contiguous layout) in memory it allocates on first use; this entry point keeps the
+// same scratch in a fixed array compiled into the library instead, so a call allocates
+// nothing.
 #include <mutex>
 
 #include "cbct_internal.cuh"
@@ -18,7 +18,8 @@ namespace cbct {
 static __device__ __align__(256) float g_static_volume[CBCT_PROJECT_STATIC_MAX_VOXELS + PROJECT_VOLUME_SLACK / 4];
 
 // In host code `g_static_volume` names a host-side stand-in, not device memory, so the
-// device address is looked up once per device (with that device current) and cached.
+// device address is looked up once per device (with that device current) and cached for
+// the life of the process (a device reset after the first call is not supported).
 constexpr int kMaxDevices = 64;
 static std::mutex g_static_mu;
 static float *g_static_ptr[kMaxDevices];

@@ -1,9 +1,11 @@
 """cbct_project_static — the projector entry point that allocates no device memory — gives
-the same projections as cbct_project, on consecutive calls that reuse its fixed scratch.
+the same projections as cbct_project, bit for bit, on consecutive calls that reuse its
+fixed scratch, and leaves the device's free memory unchanged.
 
-It serves callers that cannot allocate device memory while running, such as code that
-enqueues work during CUDA stream capture or a service whose device memory is fixed at
-start-up. This file is collected last so that a failure here leaves every other test run.
+It serves callers that cannot allocate device memory while running, such as a service
+whose device memory is fixed at start-up or a latency-critical loop that cannot afford
+the synchronisation an allocation may cause. This file is collected last so that a
+failure here leaves every other test run.
 """
 import numpy as np
 import pytest
@@ -41,6 +43,7 @@ GEOMS = [
 
 @pytest.mark.parametrize("gi", range(len(GEOMS)))
 def test_project_static_matches_project_on_repeated_calls(cb, gi):
+    """Both entry points run the same kernels on the same input: the results are equal."""
     geom = GEOMS[gi]
     f = torch.tensor(synth.random_volume(geom, 404 + gi), dtype=torch.float32, device="cuda")
     with cb.Geometry(geom) as g:
@@ -50,7 +53,26 @@ def test_project_static_matches_project_on_repeated_calls(cb, gi):
             cb.project_static(g, f, out)
             got = out.cpu().numpy()
             assert np.isfinite(got).all()
-            assert rel(got, ref) <= 1e-4, rel(got, ref)
+            assert np.array_equal(got, ref), rel(got, ref)
+
+
+def test_project_static_leaves_device_memory_unchanged(cb):
+    """After the first call on the device (which looks up the scratch's address), further
+    calls change neither the free device memory nor torch's allocator."""
+    geom = GEOMS[1]
+    f = torch.tensor(synth.random_volume(geom, 410), dtype=torch.float32, device="cuda")
+    out = torch.empty(geom.proj_shape, dtype=torch.float32, device="cuda")
+    with cb.Geometry(geom) as g:
+        cb.project_static(g, f, out)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        alloc0 = torch.cuda.memory_allocated()
+        for _ in range(3):
+            cb.project_static(g, f, out)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert torch.cuda.memory_allocated() == alloc0
+        assert free1 == free0, (free0, free1)
 
 
 def test_project_static_rejects_a_volume_beyond_its_scratch(cb):
