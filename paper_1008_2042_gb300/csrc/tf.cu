@@ -303,194 +303,142 @@ namespace cbct {
 // ------------------------------------------------------------------------------------
 // Fused shrinkage step of Algorithm A2 (steps 3-4, then step 1 of the next iteration):
 //   f_new = H(W^T T_mu W x)   and optionally   v = f_new + c (f_new - f_old).
-// A block owns a TA x TB tile of the (axis 0, axis 1) plane and marches along axis 2. For
-// every plane c' it computes the 27 coefficients on the tile plus a one-voxel halo from a
-// ring of three x planes (tile plus a two-voxel halo) in shared memory, shrinks them
-// (Eq. (2)), synthesises along axis 0 and axis 1 in shared memory, and keeps the three
-// axis-2 partial sums of the last three planes in registers to finish plane c' - 1.
-// The coefficients never leave the SM: HBM traffic is one read of x (plus halo re-reads
-// that hit L2) and the writes of f_new (and v, with one read of f_old).
+// The 27 coefficients never leave the SM: HBM traffic is one read of x (halo re-reads hit
+// L2) and the writes of f_new (and v, with one read of f_old).
+//
+// A warp covers 32 consecutive positions of one row along axis 0: the 28 output positions
+// of its tile and two halo positions on either side (the coefficients of the outputs'
+// neighbours need x one position further out). A block stacks FR_ROWS + 4 such warps along
+// axis 1 (its output rows, the two rows of coefficients around them and the two rows of x
+// those need) and marches along axis 2. Per plane every lane
+//   1. analyses along axis 2 from the three x planes it holds in registers (the next plane
+//      is loaded while this one is computed),
+//   2. along axis 1 from its neighbour rows' values through shared memory,
+//   3. along axis 0 from its neighbour lanes by shuffles, giving its position's 27
+//      coefficients, which it shrinks in registers (Eq. (2)),
+// and then synthesises back as the shrink + synthesis kernel does: shares of neighbouring
+// lanes by shuffles, of neighbouring rows through shared memory, of neighbouring planes in
+// registers, finishing the output plane one behind the analysed one.
 // ------------------------------------------------------------------------------------
-// The tile is TAF x TB (TAF = 24, 32 or 36 along axis 0, chosen per launch so that the
-// tiles cover axis 0 with the fewest idle columns: 70 = 3 x 24 - 2, 35 = 36 - 1).
-template <int TAF> struct FusedTile {
-    static constexpr int NT = TAF * TB;                      // threads
-    static constexpr int FX_A = TAF + 4, FX_B = TB + 4;      // x tile with a two-voxel halo
-    static constexpr int FA_A = TAF + 2, FA_B = TB + 2;      // coefficient tile with a one-voxel halo
-    static constexpr int FX_PLANE = FX_A * FX_B;
-    static constexpr int FA_PLANE = FA_A * FA_B;
-    static constexpr int FU_PLANE = FA_B * TAF;
-    static constexpr size_t SMEM = sizeof(float) * (3 * FX_PLANE + 27 * FA_PLANE + 9 * FU_PLANE);
-    static_assert(2 * NT >= FX_PLANE, "two x-tile positions per thread");
-};
+constexpr int FR_ROWS = 6;                       // output rows per block along axis 1
+constexpr int FR_OUT = 28;                       // output positions per warp along axis 0
+constexpr int FR_WARPS = FR_ROWS + 4;
+constexpr int FR_THREADS = 32 * FR_WARPS;
 
-template <int TAF>
-__global__ void __launch_bounds__(TAF * TB)
+__global__ void __launch_bounds__(FR_THREADS, 2)
 k_tf_shrink_fused(int n0, int n1, int n2, int chunk, const float *__restrict__ x, float mu, int positivity,
                   float *__restrict__ fnew, const float *__restrict__ fold, float coef, float *__restrict__ vout)
 {
-    using T = FusedTile<TAF>;
-    constexpr int TA = TAF, TF_THREADS = T::NT;
-    constexpr int FX_A = T::FX_A, FX_PLANE = T::FX_PLANE, FA_A = T::FA_A, FA_PLANE = T::FA_PLANE,
-                  FU_PLANE = T::FU_PLANE;
-    extern __shared__ float sm[];
-    float *sx = sm;                         // [3][FX_B][FX_A] ring of x planes
-    float *sa = sx + 3 * FX_PLANE;          // [27][FA_B][FA_A] shrunk coefficients of plane c'
-    float *su = sa + 27 * FA_PLANE;         // [9][FA_B][TA] after synthesis along axis 0
-    const int a0 = blockIdx.x * TA, b0 = blockIdx.y * TB;
+    __shared__ float s_t[2][FR_WARPS][3][32];              // axis-2 analysis of each row
+    __shared__ float s_up[2][FR_ROWS + 2][3][32], s_dn[2][FR_ROWS + 2][3][32]; // axis-1 synthesis shares
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int a_out = blockIdx.x * FR_OUT, b_out = blockIdx.y * FR_ROWS;
     const int c_begin = blockIdx.z * chunk;
     const int c_end = min(n2, c_begin + chunk);
     if (c_begin >= c_end) return;
-    const int tid = threadIdx.y * TA + threadIdx.x;
-    const int ta = threadIdx.x, tb = threadIdx.y;
-    const bool inside = a0 + ta < n0 && b0 + tb < n1;
+    const size_t plane = (size_t)n0 * n1;
+    const int pa = a_out + lane - 2, pb = b_out + w - 2;  // this lane's position (unwrapped)
+    const size_t inplane = (size_t)wrapi(pb, n1) * n0 + wrapi(pa, n0);
+    const bool coef_row = w >= 1 && w <= FR_ROWS + 2;     // rows whose coefficients are formed
+    const bool out_row = w >= 2 && w <= FR_ROWS + 1 && pb < n1;
+    const bool out_lane = lane >= 2 && lane < 2 + FR_OUT && pa < n0;
+    const float *src = x + inplane;
 
-    // in-plane source offsets of the (at most two) x-tile positions this thread loads
-    int off[2];
+    // x of this position at planes cp - 1, cp, cp + 1 (cp: the analysed plane)
+    float xm = __ldg(src + (size_t)wrapi(c_begin - 2, n2) * plane);
+    float x0 = __ldg(src + (size_t)wrapi(c_begin - 1, n2) * plane);
+    float xp = __ldg(src + (size_t)wrapi(c_begin, n2) * plane);
+    float w_m2[3] = {0.f, 0.f, 0.f}, w_m1[3] = {0.f, 0.f, 0.f}; // axis-2 synthesis inputs at cp-2, cp-1
+    int buf = 0;
+    for (int cp = c_begin - 1; cp <= c_end; ++cp, buf ^= 1) {
+        const float xn = cp < c_end ? __ldg(src + (size_t)wrapi(cp + 2, n2) * plane) : 0.0f;
+        // 1. analysis along axis 2
+        float t[3];
+        ana3(xm, x0, xp, t[0], t[1], t[2]);
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int pos = tid + k * TF_THREADS;
-        if (pos < FX_PLANE) {
-            const int r = pos / FX_A, q = pos - r * FX_A;
-            off[k] = wrapi(b0 + r - 2, n1) * n0 + wrapi(a0 + q - 2, n0);
-        } else {
-            off[k] = -1;
-        }
-    }
-    auto load_x = [&](int c, int slot) {
-        const float *src = x + (size_t)wrapi(c, n2) * n1 * n0;
-        float *d = sx + slot * FX_PLANE;
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-            if (off[k] >= 0) d[tid + k * TF_THREADS] = __ldg(src + off[k]);
-    };
-
-    // planes c' run from c_begin - 1 to c_end; the ring holds x(c'-1), x(c'), x(c'+1)
-    load_x(c_begin - 2, 0);
-    load_x(c_begin - 1, 1);
-    float w_m2[3] = {0.f, 0.f, 0.f}, w_m1[3] = {0.f, 0.f, 0.f}; // w_n at planes c'-2, c'-1
-    for (int s = 0; s <= c_end - c_begin + 1; ++s) {
-        const int cp = c_begin - 1 + s;
-        load_x(cp + 1, (s + 2) % 3);
+        for (int n = 0; n < 3; ++n) s_t[buf][w][n][lane] = t[n];
         __syncthreads();
-        const float *xm = sx + (s % 3) * FX_PLANE, *x0 = sx + ((s + 1) % 3) * FX_PLANE,
-                    *xp = sx + ((s + 2) % 3) * FX_PLANE; // planes cp-1, cp, cp+1
-        // 1. coefficients of plane cp on the tile + halo, shrunk (Eq. (2))
-        for (int pos = tid; pos < FA_PLANE; pos += TF_THREADS) {
-            const int r = pos / FA_A, q = pos - r * FA_A; // x-tile position (r + 1, q + 1)
-            float u3[3][3][3];                             // [cc][m][l]
-            const float *pl[3] = {xm, x0, xp};
+        float midn[3] = {0.f, 0.f, 0.f};
+        if (coef_row) { // warp-uniform
+            // 2. along axis 1: u[m][n]
+            float u[3][3];
 #pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-                float t[3][3];
-#pragma unroll
-                for (int bb = 0; bb < 3; ++bb) {
-                    const float *row = pl[cc] + (r + bb) * FX_A + q;
-                    ana3(row[0], row[1], row[2], t[bb][0], t[bb][1], t[bb][2]);
-                }
-#pragma unroll
-                for (int l = 0; l < 3; ++l) ana3(t[0][l], t[1][l], t[2][l], u3[cc][0][l], u3[cc][1][l], u3[cc][2][l]);
-            }
+            for (int n = 0; n < 3; ++n)
+                ana3(s_t[buf][w - 1][n][lane], t[n], s_t[buf][w + 1][n][lane], u[0][n], u[1][n], u[2][n]);
+            // 3. along axis 0: alpha[l + 3m + 9n]
             float al[27];
 #pragma unroll
             for (int m = 0; m < 3; ++m)
 #pragma unroll
-                for (int l = 0; l < 3; ++l)
-                    ana3(u3[0][m][l], u3[1][m][l], u3[2][m][l], al[l + 3 * m], al[l + 3 * m + 9], al[l + 3 * m + 18]);
+                for (int n = 0; n < 3; ++n) {
+                    const float pv = __shfl_up_sync(0xffffffffu, u[m][n], 1);
+                    const float nv = __shfl_down_sync(0xffffffffu, u[m][n], 1);
+                    ana3(pv, u[m][n], nv, al[3 * m + 9 * n], al[1 + 3 * m + 9 * n], al[2 + 3 * m + 9 * n]);
+                }
+            // vector shrinkage, Eq. (2)
             float s2 = 0.0f;
 #pragma unroll
             for (int ch = 1; ch < 27; ++ch) s2 = fmaf(al[ch], al[ch], s2);
             const float nrm = sqrtf(s2);
             const float scale = nrm > mu ? 1.0f - mu / nrm : 0.0f;
-            sa[pos] = al[0];
 #pragma unroll
-            for (int ch = 1; ch < 27; ++ch) sa[ch * FA_PLANE + pos] = al[ch] * scale;
+            for (int ch = 1; ch < 27; ++ch) al[ch] *= scale;
+            // synthesis along axis 0 (lanes), then the shares along axis 1
+            float us[9];
+#pragma unroll
+            for (int mn = 0; mn < 9; ++mn) {
+                float up, mid, dn;
+                syn_shares(al[3 * mn], al[3 * mn + 1], al[3 * mn + 2], up, mid, dn);
+                us[mn] = __shfl_up_sync(0xffffffffu, up, 1) + mid + __shfl_down_sync(0xffffffffu, dn, 1);
+            }
+#pragma unroll
+            for (int n = 0; n < 3; ++n) {
+                float up, dn;
+                syn_shares(us[3 * n], us[3 * n + 1], us[3 * n + 2], up, midn[n], dn);
+                s_up[buf][w - 1][n][lane] = up;
+                s_dn[buf][w - 1][n][lane] = dn;
+            }
         }
         __syncthreads();
-        // 2. synthesis along axis 0: u_{mn} = sum_l, for TA x (TB+2) positions
-        for (int i = tid; i < 9 * FU_PLANE; i += TF_THREADS) {
-            const int mn = i / FU_PLANE, rem = i - mn * FU_PLANE;
-            const int r = rem / TA, q = rem - r * TA;
-            const float *b0p = sa + (3 * mn) * FA_PLANE + r * FA_A + q; // l = 0
-            const float *b1p = b0p + FA_PLANE, *b2p = b1p + FA_PLANE;
-            su[i] = syn3(b0p[0], b0p[1], b0p[2], b1p[0], b1p[2], b2p[0], b2p[1], b2p[2]);
-        }
-        __syncthreads();
-        // 3. synthesis along axis 1: w_n = sum_m
-        float w[3];
+        if (out_row) {
+            float wv[3];
 #pragma unroll
-        for (int n = 0; n < 3; ++n) {
-            const float *m0 = su + (3 * n + 0) * FU_PLANE + tb * TA + ta;
-            const float *m1 = m0 + FU_PLANE, *m2 = m1 + FU_PLANE;
-            w[n] = syn3(m0[0], m0[TA], m0[2 * TA], m1[0], m1[2 * TA], m2[0], m2[TA], m2[2 * TA]);
-        }
-        // 4. synthesis along axis 2 gives plane cp - 1; positivity; momentum point
-        if (s >= 2 && inside) {
-            float o = syn3(w_m2[0], w_m1[0], w[0], w_m2[1], w[1], w_m2[2], w_m1[2], w[2]);
-            if (positivity && o < 0.0f) o = 0.0f;
-            const size_t idx = ((size_t)(cp - 1) * n1 + (b0 + tb)) * n0 + (a0 + ta);
-            fnew[idx] = o;
-            if (vout) vout[idx] = fmaf(coef, o - __ldg(fold + idx), o);
-        }
+            for (int n = 0; n < 3; ++n) wv[n] = s_up[buf][w - 2][n][lane] + midn[n] + s_dn[buf][w][n][lane];
+            // synthesis along axis 2: plane cp - 1 from planes cp - 2, cp - 1, cp
+            if (cp >= c_begin + 1 && out_lane) {
+                float o = syn3(w_m2[0], w_m1[0], wv[0], w_m2[1], wv[1], w_m2[2], w_m1[2], wv[2]);
+                if (positivity && o < 0.0f) o = 0.0f;
+                const size_t idx = (size_t)(cp - 1) * plane + (size_t)pb * n0 + pa;
+                fnew[idx] = o;
+                if (vout) vout[idx] = fmaf(coef, o - __ldg(fold + idx), o);
+            }
 #pragma unroll
-        for (int n = 0; n < 3; ++n) {
-            w_m2[n] = w_m1[n];
-            w_m1[n] = w[n];
+            for (int n = 0; n < 3; ++n) {
+                w_m2[n] = w_m1[n];
+                w_m1[n] = wv[n];
+            }
         }
-        __syncthreads();
+        xm = x0;
+        x0 = xp;
+        xp = xn;
     }
 }
 
-template <int TAF> static std::atomic<unsigned long long> g_fused_optin{0};
-
-template <int TAF> static cbct_status fused_optin()
-{
-    cudaError_t e = smem_optin_once(k_tf_shrink_fused<TAF>, (int)FusedTile<TAF>::SMEM, g_fused_optin<TAF>);
-    return e == cudaSuccess ? CBCT_OK : check_cuda(e, "tf_shrink_fused attribute");
-}
-
-cbct_status tf_prepare()
-{
-    cbct_status r = fused_optin<24>();
-    if (r == CBCT_OK) r = fused_optin<32>();
-    if (r == CBCT_OK) r = fused_optin<36>();
-    return r;
-}
-
-template <int TAF>
-static cbct_status launch_fused_t(int n0, int n1, int n2, const float *x, float mu, int positivity, float *fnew,
-                                  const float *fold, float coef, float *vout, cudaStream_t st)
-{
-    cbct_status a = fused_optin<TAF>();
-    if (a != CBCT_OK) return a;
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tf_shrink_fused<TAF>, TAF * TB,
-                                                                  FusedTile<TAF>::SMEM);
-    if (e != cudaSuccess) return check_cuda(e, "tf_shrink_fused occupancy");
-    const long long tiles = (long long)((n0 + TAF - 1) / TAF) * ((n1 + TB - 1) / TB);
-    const int chunk = fused_chunk(tiles, n2, (per_sm > 0 ? per_sm : 1) * device_sm_count());
-    dim3 grid((n0 + TAF - 1) / TAF, (n1 + TB - 1) / TB, (n2 + chunk - 1) / chunk);
-    CBCT_TIMED(CBCT_KERNEL_TF_SYNTH, st,
-               k_tf_shrink_fused<TAF><<<grid, dim3(TAF, TB), FusedTile<TAF>::SMEM, st>>>(
-                   n0, n1, n2, chunk, x, mu, positivity, fnew, fold, coef, vout));
-    return check_cuda(cudaGetLastError(), "tf_shrink_fused launch");
-}
+cbct_status tf_prepare() { return CBCT_OK; }
 
 cbct_status launch_tf_shrink_fused(int n0, int n1, int n2, const float *x, float mu, int positivity, float *fnew,
                                    const float *fold, float coef, float *vout, cudaStream_t st)
 {
-    // the tile width covering axis 0 with the fewest columns (ties: the narrower tile)
-    int taf = 24, cover = ((n0 + 23) / 24) * 24;
-    for (int w : {32, 36}) {
-        const int c = ((n0 + w - 1) / w) * w;
-        if (c < cover) {
-            cover = c;
-            taf = w;
-        }
-    }
-    if (taf == 32) return launch_fused_t<32>(n0, n1, n2, x, mu, positivity, fnew, fold, coef, vout, st);
-    if (taf == 36) return launch_fused_t<36>(n0, n1, n2, x, mu, positivity, fnew, fold, coef, vout, st);
-    return launch_fused_t<24>(n0, n1, n2, x, mu, positivity, fnew, fold, coef, vout, st);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tf_shrink_fused, FR_THREADS, 0);
+    if (e != cudaSuccess) return check_cuda(e, "tf_shrink_fused occupancy");
+    const long long tiles = (long long)((n0 + FR_OUT - 1) / FR_OUT) * ((n1 + FR_ROWS - 1) / FR_ROWS);
+    const int chunk = fused_chunk(tiles, n2, (per_sm > 0 ? per_sm : 1) * device_sm_count());
+    dim3 grid((n0 + FR_OUT - 1) / FR_OUT, (n1 + FR_ROWS - 1) / FR_ROWS, (n2 + chunk - 1) / chunk);
+    CBCT_TIMED(CBCT_KERNEL_TF_SYNTH, st,
+               k_tf_shrink_fused<<<grid, dim3(32, FR_WARPS), 0, st>>>(n0, n1, n2, chunk, x, mu, positivity, fnew, fold,
+                                                                      coef, vout));
+    return check_cuda(cudaGetLastError(), "tf_shrink_fused launch");
 }
 
 } // namespace cbct
