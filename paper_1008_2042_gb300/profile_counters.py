@@ -84,7 +84,9 @@ def main(argv=None):
     ap.add_argument("--logdir", default=os.path.join(HERE, "_build", "ncu"), help="where the raw ncu CSV logs go")
     a = ap.parse_args(argv)
     os.makedirs(a.logdir, exist_ok=True)
-    rec = {"_comment": __doc__.strip().splitlines()[0] + " See paper_1008_2042_gb300/profile_counters.py."}
+    rec = {"_comment": "Per-launch Nsight Compute counters of P and P^T on every multigrid level of the paper-scale "
+                       "workload (one launch per level); written by paper_1008_2042_gb300/profile_counters.py, used "
+                       "by bench.py while the kernel sources hash to sources_sha256."}
     for kernel in KERNEL_SOURCES:
         levels = {}
         for lev in LEVELS:
