@@ -42,15 +42,6 @@ __device__ __forceinline__ float syn3(float P0, float C0, float N0, float P1, fl
     return fmaf(0.25f, (P0 + N0) - (P2 + N2), fmaf(0.5f, C0 + C2, R2_4 * (P1 - N1)));
 }
 
-static int tf_chunk(int n0, int n1, int n2)
-{
-    const long long tiles = (long long)((n0 + TA - 1) / TA) * ((n1 + TB - 1) / TB);
-    const long long want = 6LL * device_sm_count();
-    long long nch = (want + tiles - 1) / tiles;
-    if (nch < 1) nch = 1;
-    if (nch > n2) nch = n2;
-    return (int)((n2 + nch - 1) / nch);
-}
 
 template <typename TA_T>
 __global__ void __launch_bounds__(TF_THREADS)
@@ -75,21 +66,32 @@ k_tf_analyze(int n0, int n1, int n2, int chunk, const float *__restrict__ f, TA_
             off[k] = -1;
         }
     }
-    auto load_plane = [&](int c, int slot) {
+    // the haloed tile of plane c: this thread's (at most two) values
+    float nxt[2] = {0.0f, 0.0f};
+    auto fetch = [&](int c) {
         const float *src = f + (size_t)wrapi(c, n2) * n1 * n0;
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            if (off[k] >= 0) nxt[k] = __ldg(src + off[k]);
+    };
+    auto put = [&](int slot) {
         float *d = &s[slot][0][0];
 #pragma unroll
         for (int k = 0; k < 2; ++k)
-            if (off[k] >= 0) d[tid + k * TF_THREADS] = __ldg(src + off[k]);
+            if (off[k] >= 0) d[tid + k * TF_THREADS] = nxt[k];
     };
-    load_plane(c_begin - 1, 0);
-    load_plane(c_begin, 1);
+    fetch(c_begin - 1);
+    put(0);
+    fetch(c_begin);
+    put(1);
+    fetch(c_begin + 1);
     const int ta = threadIdx.x, tb = threadIdx.y;
     const bool inside = a0 + ta < n0 && b0 + tb < n1;
     for (int c = c_begin; c < c_end; ++c) {
         const int j = c - c_begin;
-        load_plane(c + 1, (j + 2) % 3);
+        put((j + 2) % 3); // plane c + 1, loaded during the previous plane
         __syncthreads();
+        if (c + 1 < c_end) fetch(c + 2); // lands while this plane is computed and stored
         if (inside) {
             const int sl[3] = {j % 3, (j + 1) % 3, (j + 2) % 3}; // planes c-1, c, c+1
             // axis 0 then axis 1: u[cc][m][l]
@@ -255,20 +257,24 @@ k_tf_synth_shrink(int n0, int n1, int n2, int chunk, const TA_T *__restrict__ al
     }
 }
 
+template <typename TA_T>
+static cbct_status launch_tf_analyze_t(int n0, int n1, int n2, const float *f, TA_T *alpha, cudaStream_t st)
+{
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tf_analyze<TA_T>, TF_THREADS, 0);
+    if (e != cudaSuccess) return check_cuda(e, "tf_analyze occupancy");
+    const long long tiles = (long long)((n0 + TA - 1) / TA) * ((n1 + TB - 1) / TB);
+    const int chunk = fused_chunk(tiles, n2, (per_sm > 0 ? per_sm : 1) * device_sm_count());
+    dim3 grid((n0 + TA - 1) / TA, (n1 + TB - 1) / TB, (n2 + chunk - 1) / chunk);
+    CBCT_TIMED(CBCT_KERNEL_TF_ANALYZE, st, k_tf_analyze<<<grid, dim3(TA, TB), 0, st>>>(n0, n1, n2, chunk, f, alpha));
+    return check_cuda(cudaGetLastError(), "tf_analyze launch");
+}
+
 cbct_status launch_tf_analyze(int n0, int n1, int n2, const float *f, void *alpha, cudaStream_t st, int storage)
 {
-    const int chunk = tf_chunk(n0, n1, n2);
-    dim3 grid((n0 + TA - 1) / TA, (n1 + TB - 1) / TB, (n2 + chunk - 1) / chunk);
-    if (storage == ST_BF16)
-        CBCT_TIMED(CBCT_KERNEL_TF_ANALYZE, st,
-                   k_tf_analyze<<<grid, dim3(TA, TB), 0, st>>>(n0, n1, n2, chunk, f, static_cast<__nv_bfloat16 *>(alpha)));
-    else if (storage == ST_F16)
-        CBCT_TIMED(CBCT_KERNEL_TF_ANALYZE, st,
-                   k_tf_analyze<<<grid, dim3(TA, TB), 0, st>>>(n0, n1, n2, chunk, f, static_cast<__half *>(alpha)));
-    else
-        CBCT_TIMED(CBCT_KERNEL_TF_ANALYZE, st,
-                   k_tf_analyze<<<grid, dim3(TA, TB), 0, st>>>(n0, n1, n2, chunk, f, static_cast<float *>(alpha)));
-    return check_cuda(cudaGetLastError(), "tf_analyze launch");
+    if (storage == ST_BF16) return launch_tf_analyze_t(n0, n1, n2, f, static_cast<__nv_bfloat16 *>(alpha), st);
+    if (storage == ST_F16) return launch_tf_analyze_t(n0, n1, n2, f, static_cast<__half *>(alpha), st);
+    return launch_tf_analyze_t(n0, n1, n2, f, static_cast<float *>(alpha), st);
 }
 
 template <typename TA_T>
