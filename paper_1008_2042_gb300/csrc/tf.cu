@@ -277,10 +277,157 @@ cbct_status launch_tf_analyze(int n0, int n1, int n2, const float *f, void *alph
     return launch_tf_analyze_t(n0, n1, n2, f, static_cast<float *>(alpha), st);
 }
 
+// The same step for 16-bit coefficients with two adjacent positions per lane: each
+// channel is one 4-byte load of the pair, and one pair of shuffles per channel group
+// serves both positions (the pair's inner shares stay in the lane). A warp covers 64
+// positions: 60 outputs, the halo position on either side and one unused position at each
+// end, so that every pair starts on an even position (4-byte aligned when the contiguous
+// extent n0 is even, which the launcher requires; an even n0 also keeps a pair from
+// straddling the periodic wrap).
+constexpr int SP_OUT = 60;
+constexpr int SP_ROWS = 6;                      // output rows per block
+constexpr int SP_WARPS = SP_ROWS + 2;
+constexpr int SP_THREADS = 32 * SP_WARPS;
+
+template <typename T16> struct Pair16;
+template <> struct Pair16<__nv_bfloat16> {
+    using T2 = __nv_bfloat162;
+    static __device__ __forceinline__ float2 f2(T2 v) { return __bfloat1622float2(v); }
+};
+template <> struct Pair16<__half> {
+    using T2 = __half2;
+    static __device__ __forceinline__ float2 f2(T2 v) { return __half22float2(v); }
+};
+
+template <typename T16>
+__global__ void __launch_bounds__(SP_THREADS, 2)
+k_tf_synth_shrink_pair(int n0, int n1, int n2, int chunk, const T16 *__restrict__ alpha, float mu, int positivity,
+                       float *__restrict__ f)
+{
+    using P = Pair16<T16>;
+    using T2 = typename P::T2;
+    __shared__ float2 s_up[2][SP_WARPS][3][32], s_dn[2][SP_WARPS][3][32];
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int a_out = blockIdx.x * SP_OUT, b_out = blockIdx.y * SP_ROWS;
+    const int c_begin = blockIdx.z * chunk;
+    const int c_end = min(n2, c_begin + chunk);
+    if (c_begin >= c_end) return;
+    const size_t N = (size_t)n0 * n1 * n2;
+    const size_t plane = (size_t)n0 * n1;
+    const int pa = a_out - 2 + 2 * lane, pb = b_out + w - 1; // the pair (pa, pa + 1), unwrapped
+    const size_t inplane = (size_t)wrapi(pb, n1) * n0 + wrapi(pa, n0);
+    const bool out_lane = lane >= 1 && lane <= SP_OUT / 2 && pa < n0; // n0 even: pa + 1 < n0 too
+    const bool out_row = w >= 1 && w <= SP_ROWS && pb < n1;
+
+    T2 nxt[27];
+    auto fetch = [&](int c) {
+        const T2 *src = reinterpret_cast<const T2 *>(alpha + (size_t)wrapi(c, n2) * plane + inplane);
+        const size_t stride = N / 2; // channels in pairs (N is even)
+#pragma unroll
+        for (int ch = 0; ch < 27; ++ch) nxt[ch] = src[(size_t)ch * stride];
+    };
+    fetch(c_begin - 1);
+    float2 w_m2[3], w_m1[3];
+#pragma unroll
+    for (int n = 0; n < 3; ++n) w_m2[n] = w_m1[n] = make_float2(0.f, 0.f);
+    int buf = 0;
+    for (int cp = c_begin - 1; cp <= c_end; ++cp, buf ^= 1) {
+        T2 cur[27];
+#pragma unroll
+        for (int ch = 0; ch < 27; ++ch) cur[ch] = nxt[ch];
+        if (cp < c_end) fetch(cp + 1);
+        // vector shrinkage, Eq. (2), for both positions
+        float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int ch = 1; ch < 27; ++ch) {
+            const float2 a = P::f2(cur[ch]);
+            s2.x = fmaf(a.x, a.x, s2.x);
+            s2.y = fmaf(a.y, a.y, s2.y);
+        }
+        const float na = sqrtf(s2.x), nb = sqrtf(s2.y);
+        const float sa = na > mu ? 1.0f - mu / na : 0.0f, sb = nb > mu ? 1.0f - mu / nb : 0.0f;
+        // axis 0: position A (even) takes lane - 1's B and its own B; B takes its own A and
+        // lane + 1's A
+        float2 u[9];
+#pragma unroll
+        for (int mn = 0; mn < 9; ++mn) {
+            float2 a0 = P::f2(cur[3 * mn]), a1 = P::f2(cur[3 * mn + 1]), a2 = P::f2(cur[3 * mn + 2]);
+            if (mn) {
+                a0.x *= sa;
+                a0.y *= sb;
+            }
+            a1.x *= sa;
+            a1.y *= sb;
+            a2.x *= sa;
+            a2.y *= sb;
+            float upA, midA, dnA, upB, midB, dnB;
+            syn_shares(a0.x, a1.x, a2.x, upA, midA, dnA);
+            syn_shares(a0.y, a1.y, a2.y, upB, midB, dnB);
+            u[mn].x = __shfl_up_sync(0xffffffffu, upB, 1) + midA + dnB;
+            u[mn].y = upA + midB + __shfl_down_sync(0xffffffffu, dnA, 1);
+        }
+        // axis 1 (warps) through shared memory
+        float2 midn[3];
+#pragma unroll
+        for (int n = 0; n < 3; ++n) {
+            float2 up, dn;
+            syn_shares(u[3 * n].x, u[3 * n + 1].x, u[3 * n + 2].x, up.x, midn[n].x, dn.x);
+            syn_shares(u[3 * n].y, u[3 * n + 1].y, u[3 * n + 2].y, up.y, midn[n].y, dn.y);
+            s_up[buf][w][n][lane] = up;
+            s_dn[buf][w][n][lane] = dn;
+        }
+        __syncthreads();
+        if (out_row) {
+            float2 wv[3];
+#pragma unroll
+            for (int n = 0; n < 3; ++n) {
+                const float2 a = s_up[buf][w - 1][n][lane], b = s_dn[buf][w + 1][n][lane];
+                wv[n] = make_float2(a.x + midn[n].x + b.x, a.y + midn[n].y + b.y);
+            }
+            if (cp >= c_begin + 1 && out_lane) {
+                float2 o;
+                o.x = syn3(w_m2[0].x, w_m1[0].x, wv[0].x, w_m2[1].x, wv[1].x, w_m2[2].x, w_m1[2].x, wv[2].x);
+                o.y = syn3(w_m2[0].y, w_m1[0].y, wv[0].y, w_m2[1].y, wv[1].y, w_m2[2].y, w_m1[2].y, wv[2].y);
+                if (positivity) {
+                    o.x = o.x < 0.0f ? 0.0f : o.x;
+                    o.y = o.y < 0.0f ? 0.0f : o.y;
+                }
+                *reinterpret_cast<float2 *>(f + (size_t)(cp - 1) * plane + (size_t)pb * n0 + pa) = o;
+            }
+#pragma unroll
+            for (int n = 0; n < 3; ++n) {
+                w_m2[n] = w_m1[n];
+                w_m1[n] = wv[n];
+            }
+        }
+    }
+}
+
+template <typename T16>
+static cbct_status launch_tf_synth_shrink_pair(int n0, int n1, int n2, const T16 *alpha, float mu, int positivity,
+                                               float *f, cudaStream_t st)
+{
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tf_synth_shrink_pair<T16>, SP_THREADS, 0);
+    if (e != cudaSuccess) return check_cuda(e, "tf_synth_shrink occupancy");
+    const long long tiles = (long long)((n0 + SP_OUT - 1) / SP_OUT) * ((n1 + SP_ROWS - 1) / SP_ROWS);
+    const int chunk = fused_chunk(tiles, n2, (per_sm > 0 ? per_sm : 1) * device_sm_count());
+    dim3 grid((n0 + SP_OUT - 1) / SP_OUT, (n1 + SP_ROWS - 1) / SP_ROWS, (n2 + chunk - 1) / chunk);
+    CBCT_TIMED(CBCT_KERNEL_TF_SYNTH, st,
+               k_tf_synth_shrink_pair<T16><<<grid, dim3(32, SP_WARPS), 0, st>>>(n0, n1, n2, chunk, alpha, mu, positivity,
+                                                                                f));
+    return check_cuda(cudaGetLastError(), "tf_synth_shrink launch");
+}
+
 template <typename TA_T>
 static cbct_status launch_tf_synth_shrink_t(int n0, int n1, int n2, const TA_T *alpha, float mu, int positivity,
                                             float *f, cudaStream_t st)
 {
+    // 16-bit coefficients of an even contiguous extent: two positions per lane (aligned pairs;
+    // the array's base is at least 4-byte aligned, as for any 16-bit tensor the API accepts)
+    if constexpr (sizeof(TA_T) == 2)
+        if (n0 % 2 == 0 && (reinterpret_cast<uintptr_t>(alpha) & 3) == 0 && (reinterpret_cast<uintptr_t>(f) & 7) == 0)
+            return launch_tf_synth_shrink_pair(n0, n1, n2, alpha, mu, positivity, f, st);
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tf_synth_shrink<TA_T>, SY_THREADS, 0);
     if (e != cudaSuccess) return check_cuda(e, "tf_synth_shrink occupancy");
