@@ -25,28 +25,6 @@
 
 namespace cbct {
 
-__device__ __forceinline__ int lower_count(const float *a, int n, float t) // # a[i] < t
-{
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a[mid] < t) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int upper_count(const float *a, int n, float t) // # a[i] <= t
-{
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a[mid] <= t) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
 // 16-byte asynchronous global -> shared copy (L2 only); both addresses 16-byte aligned
 __device__ __forceinline__ void cp_async16(float *smem_dst, const float *gsrc)
 {
@@ -105,30 +83,39 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
     const int sxs = dxr > 0.0f ? 1 : -1, sys = dyr > 0.0f ? 1 : -1;
 
     // ---- phase 1: crossings of each plane family, then their merged order ----
-    int a_le = 0, a_in = 0, b_le = 0, b_in = 0;
-    for (int a0 = 0; a0 <= G.nx; a0 += nthr) {
-        const int a = a0 + tid;
-        bool le = false, in = false;
-        if (a <= G.nx && hit && dxr != 0.0f) {
+    // counts of the crossings before the entry point and inside the volume: per thread, then
+    // one block-wide sum (the lists are written before the barrier of that sum)
+    unsigned cnt4[4] = {0u, 0u, 0u, 0u}; // a_le, a_in, b_le, b_in
+    for (int a = tid; a <= G.nx; a += nthr) {
+        if (hit && dxr != 0.0f) {
             const float t = tau_plane(plane_at(dxr > 0.0f ? a : G.nx - a, G.dx, G.x0), qx, inv_x);
             sA[a] = t;
-            le = t <= tau_in;
-            in = t > tau_in && t < tau_out;
+            cnt4[0] += t <= tau_in;
+            cnt4[1] += t > tau_in && t < tau_out;
         }
-        a_le += __syncthreads_count(le);
-        a_in += __syncthreads_count(in);
     }
-    for (int b0 = 0; b0 <= G.ny; b0 += nthr) {
-        const int b = b0 + tid;
-        bool le = false, in = false;
-        if (b <= G.ny && hit && dyr != 0.0f) {
+    for (int b = tid; b <= G.ny; b += nthr) {
+        if (hit && dyr != 0.0f) {
             const float t = tau_plane(plane_at(dyr > 0.0f ? b : G.ny - b, G.dy, G.y0), qy, inv_y);
             sB[b] = t;
-            le = t <= tau_in;
-            in = t > tau_in && t < tau_out;
+            cnt4[2] += t <= tau_in;
+            cnt4[3] += t > tau_in && t < tau_out;
         }
-        b_le += __syncthreads_count(le);
-        b_in += __syncthreads_count(in);
+    }
+    // per-warp sums, parked in the segment records (written only after the merge below)
+    unsigned *s_cnt = reinterpret_cast<unsigned *>(sSeg);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const unsigned v = __reduce_add_sync(0xffffffffu, cnt4[q]);
+        if ((tid & 31) == 0) s_cnt[4 * (tid >> 5) + q] = v;
+    }
+    __syncthreads();
+    int a_le = 0, a_in = 0, b_le = 0, b_in = 0;
+    for (int wq = 0; wq < (nthr + 31) / 32; ++wq) {
+        a_le += (int)s_cnt[4 * wq + 0];
+        a_in += (int)s_cnt[4 * wq + 1];
+        b_le += (int)s_cnt[4 * wq + 2];
+        b_in += (int)s_cnt[4 * wq + 3];
     }
     const float *LA = sA + a_le, *LB = sB + b_le;
     const int nA = a_in, nB = b_in, nseg = nA + nB + 1;
@@ -139,16 +126,36 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
     const float tm = 0.5f * (tau_in + e0);
     const int ix_e = min(max((int)floorf((fmaf(tm, dxr, qx) - G.x0) / G.dx), 0), G.nx - 1);
     const int iy_e = min(max((int)floorf((fmaf(tm, dyr, qy) - G.y0) / G.dy), 0), G.ny - 1);
+    // The rank of a crossing in the other family's list: the planes of that family the ray has
+    // passed at t, estimated from its transverse position and then moved to the exact count
+    // (# LB[j] < t for an x crossing, # LA[i] <= t for a y crossing), which the lists decide.
+    auto passed = [&](float pos, float o, float inv_h, int n, int sgn, int le) {
+        const int k = (int)floorf((pos - o) * inv_h); // the plane at or below pos
+        return sgn > 0 ? k + 1 - le : n - k - le;
+    };
+    const float inv_dx = 1.0f / G.dx, inv_dy = 1.0f / G.dy;
     for (int i = tid; i < nA; i += nthr) {
         const float t = LA[i];
-        const int nb = lower_count(LB, nB, t), r = i + nb;
+        int nb = 0;
+        if (nB) {
+            nb = min(max(passed(fmaf(t, dyr, qy), G.y0, inv_dy, G.ny, sys, b_le), 0), nB);
+            while (nb > 0 && !(LB[nb - 1] < t)) --nb;
+            while (nb < nB && LB[nb] < t) ++nb;
+        }
+        const int r = i + nb;
         const int cx = min(max(ix_e + sxs * (i + 1), 0), G.nx - 1), cy = min(max(iy_e + sys * nb, 0), G.ny - 1);
         sEnd[r] = t;
         sCol[r + 1] = cx * sx + cy * sy;
     }
     for (int j = tid; j < nB; j += nthr) {
         const float t = LB[j];
-        const int na = upper_count(LA, nA, t), r = j + na;
+        int na = 0;
+        if (nA) {
+            na = min(max(passed(fmaf(t, dxr, qx), G.x0, inv_dx, G.nx, sxs, a_le), 0), nA);
+            while (na > 0 && LA[na - 1] > t) --na;
+            while (na < nA && LA[na] <= t) ++na;
+        }
+        const int r = j + na;
         const int cx = min(max(ix_e + sxs * na, 0), G.nx - 1), cy = min(max(iy_e + sys * (j + 1), 0), G.ny - 1);
         sEnd[r] = t;
         sCol[r + 1] = cx * sx + cy * sy;
@@ -247,7 +254,6 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
             cp_async_commit();
         };
         const bool split = nthr >= 2 * G.nz;
-        const float inv_dx = 1.0f / G.dx, inv_dy = 1.0f / G.dy;
         // T[k][u]: the table entry, plus the first half's total for a second-half entry
         auto tab = [&](int k, int u) {
             const float *trow = sTab + k * TPITCH;
