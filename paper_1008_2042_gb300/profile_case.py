@@ -3,7 +3,8 @@ Nsight Compute captures and quick timings of a single kernel.
 
     python -m paper_1008_2042_gb300.profile_case --op project --shape paper --repeat 3
 
---op: project | backproject | tf_analyze | tf_synth | tf_shrink (fused W, T_mu, W^T, H) | reconstruct
+--op: project | backproject | tf_analyze | tf_synth | tf_shrink (fused W, T_mu, W^T, H) | tf_shrink_z (the
+     same on the z-fastest layout the reconstruction iterates in) | reconstruct
 --shape: paper (512x512x70, 512x384 imager, 40 views) | small (64x64x16, 128x32, 40 views)
          | iso256 (256x256x64 at 1 mm, 256x192 imager at 1.5 mm, 60 views)
 --level: multigrid level of the operator's grid (0 = finest; project/backproject only)
@@ -31,7 +32,7 @@ from paper_1008_2042_gb300 import build as cuda_build  # noqa: E402
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--op", default="project",
-                    choices=("project", "backproject", "tf_analyze", "tf_synth", "tf_shrink", "reconstruct"))
+                    choices=("project", "backproject", "tf_analyze", "tf_synth", "tf_shrink", "tf_shrink_z", "reconstruct"))
     ap.add_argument("--shape", default="paper", choices=("paper", "small", "iso256"))
     ap.add_argument("--views", type=int, default=40)
     ap.add_argument("--level", type=int, default=0)
@@ -54,6 +55,9 @@ def main(argv=None):
     y = torch.rand(geom.proj_shape, device=dev, generator=rng)
     alpha = None
     f_out = torch.empty_like(f)
+    if a.op == "tf_shrink_z":  # (ny, nx, nz): z fastest, as inside the iteration
+        f = torch.rand((geom.ny, geom.nx, geom.nz), device=dev, generator=rng)
+        f_out = torch.empty_like(f)
     if a.op == "tf_synth":
         alpha = cb.tf_analyze(f)
 
@@ -66,7 +70,7 @@ def main(argv=None):
             cb.tf_analyze(f)
         elif a.op == "tf_synth":
             cb.tf_synthesize_shrink(alpha, 1e-3, True)
-        elif a.op == "tf_shrink":
+        elif a.op in ("tf_shrink", "tf_shrink_z"):
             cb.tf_shrink(f, 1e-3, True, out=f_out)
         else:
             cb.reconstruct(g, y, 5e-4, 1, [1])
