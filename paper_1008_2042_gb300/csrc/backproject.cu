@@ -23,19 +23,20 @@
 
 namespace cbct {
 
-// Thread mapping: a block of 128 threads owns a BP_BX x BP_BY tile of voxel columns; each
-// warp takes a BP_WX x (32 / BP_WX) patch of it. Lanes whose columns are close in both x
+// Thread mapping: each warp takes an 8 x 4 patch of voxel columns, and a block of NT
+// threads stacks them into a 16 x (NT / 8) tile. Lanes whose columns are close in both x
 // and y read nearby table entries in every view (a voxel's imager column moves with x at
-// some views and with y at others): an 8 x 4 patch touches 4.5 sectors per table request
-// where a 32 x 1 row touches 15.9, and the four warps of a block share their lines in L1.
-#ifndef CBCT_BP_WX
-#define CBCT_BP_WX 8
-#endif
-constexpr int BP_THREADS = 128;
-constexpr int BP_WX = CBCT_BP_WX, BP_WY = 32 / BP_WX;     // warp patch
-constexpr int BP_WPX = BP_WX == 8 ? 2 : 1, BP_WPY = 4 / BP_WPX; // warps per block along x, y
-constexpr int BP_BX = BP_WX * BP_WPX, BP_BY = BP_WY * BP_WPY;  // block tile
-static_assert(BP_WX * BP_WY == 32 && BP_WPX * BP_WPY * 32 == BP_THREADS, "block tiling");
+// some views and with y at others): an 8 x 4 patch touches 10 sectors per table request
+// where a 32 x 1 row touched 16, and the warps of a block share their lines in L1. Blocks
+// of 256 threads (16 x 16 columns) share more of each view's table lines than blocks of
+// 128 and pay where the grid is large (16-voxel chunks: 1.80 -> 1.72 ms for the paper's
+// finest grid); on coarser grids they leave too few blocks, and 128 threads are kept.
+constexpr int BP_THREADS = 128;                 // the block size of the coarser grids
+constexpr int BP_BIG_THREADS = 256;             // with 16-voxel chunks
+constexpr int BP_WX = 8, BP_WY = 4;             // warp patch
+constexpr int BP_BX = 16;                       // block tile along x (two patches)
+template <int NT> constexpr int bp_by() { return BP_WY * (NT / 64); } // block tile along y
+constexpr int BP_BY = bp_by<BP_THREADS>();
 
 // resident blocks per SM the register budget of the 16-voxel chunks is sized for (64
 // registers, no spills)
@@ -65,10 +66,14 @@ int backproject_max_blocks(const GeomDev &G)
     return ((G.nx + BP_BX - 1) / BP_BX) * ((G.ny + BP_BY - 1) / BP_BY) * G.nz; // one z voxel per thread
 }
 
+// threads per block of a launch with z chunk zc
+static int bp_threads(int zc) { return zc >= 16 ? BP_BIG_THREADS : BP_THREADS; }
+
 int backproject_num_blocks(const GeomDev &G)
 {
     const int zc = bp_zchunk(G);
-    return ((G.nx + BP_BX - 1) / BP_BX) * ((G.ny + BP_BY - 1) / BP_BY) * ((G.nz + zc - 1) / zc);
+    const int by = bp_threads(zc) == BP_BIG_THREADS ? bp_by<BP_BIG_THREADS>() : BP_BY;
+    return ((G.nx + BP_BX - 1) / BP_BX) * ((G.ny + by - 1) / by) * ((G.nz + zc - 1) / zc);
 }
 
 // Rows whose ray, while inside the column (tau in [ta, tb], 1/(tc+ta) = A, 1/(tc+tb) = B),
@@ -133,22 +138,22 @@ __device__ __forceinline__ void plane_window(const GeomDev &G, float zp, float A
 #ifndef CBCT_BP_MIN_BLOCKS
 #define CBCT_BP_MIN_BLOCKS 9
 #endif
-template <int ZC, bool FLAT>
-__global__ void __launch_bounds__(BP_THREADS, ZC >= 16 ? CBCT_BP_Z16_BLOCKS : ZC >= 8 ? CBCT_BP_MIN_BLOCKS : 1)
+template <int ZC, bool FLAT, int NT>
+__global__ void __launch_bounds__(NT, ZC >= 16 ? CBCT_BP_Z16_BLOCKS * 128 / NT : ZC >= 8 ? CBCT_BP_MIN_BLOCKS : 1)
 k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out, int sx, int sy, int sz,
               float *__restrict__ out2, double *__restrict__ partials)
 {
     extern __shared__ float s_invv[]; // 1 / v per imager row
-    __shared__ double s_warp[BP_THREADS / 32];
+    __shared__ double s_warp[NT / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < G.nv; i += BP_THREADS) {
+    for (int i = tid; i < G.nv; i += NT) {
         const float v = imager_v(G, i);
         s_invv[i] = v != 0.0f ? __frcp_rn(v) : 1e30f;
     }
     __syncthreads();
 
-    const int ix = blockIdx.x * BP_BX + (warp % BP_WPX) * BP_WX + lane % BP_WX;
-    const int iy = blockIdx.y * BP_BY + (warp / BP_WPX) * BP_WY + lane / BP_WX;
+    const int ix = blockIdx.x * BP_BX + (warp & 1) * BP_WX + lane % BP_WX;
+    const int iy = blockIdx.y * bp_by<NT>() + (warp >> 1) * BP_WY + lane / BP_WX;
     const int iz0 = blockIdx.z * ZC;
     const bool ok = ix < G.nx && iy < G.ny;
     float acc[ZC];
@@ -339,7 +344,7 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
         __syncthreads();
         if (tid == 0) {
             double t = 0.0;
-            for (int w = 0; w < BP_THREADS / 32; ++w) t += s_warp[w];
+            for (int w = 0; w < NT / 32; ++w) t += s_warp[w];
             partials[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
         }
     }
@@ -349,23 +354,25 @@ cbct_status launch_backproject(const GeomDev &G, const float2 *ps, float *out, l
                                long long sz, float *out2, double *partials, cudaStream_t st)
 {
     const int zc = bp_zchunk(G);
-    dim3 block(BP_THREADS);
-    dim3 grid((G.nx + BP_BX - 1) / BP_BX, (G.ny + BP_BY - 1) / BP_BY, (G.nz + zc - 1) / zc);
+    const int nt = bp_threads(zc);
+    const int by = nt == BP_BIG_THREADS ? bp_by<BP_BIG_THREADS>() : BP_BY;
+    dim3 block(nt);
+    dim3 grid((G.nx + BP_BX - 1) / BP_BX, (G.ny + by - 1) / by, (G.nz + zc - 1) / zc);
     const size_t smem = sizeof(float) * G.nv;
     const int isx = (int)sx, isy = (int)sy, isz = (int)sz;
     ProfToken tok = prof_start(CBCT_KERNEL_BACKPROJECT, st);
     // flatten the candidate loop where a voxel column's shadow spans about one imager
     // column (its diagonal, magnified at the rotation axis, below 1.5 pixels)
     const bool flat = sqrtf(G.dx * G.dx + G.dy * G.dy) * (G.sdd / G.sad) < 1.5f * G.du;
-#define CBCT_BP_LAUNCH(Z)                                                                                 \
-    if (flat) k_backproject<Z, true><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials); \
-    else k_backproject<Z, false><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials)
+#define CBCT_BP_LAUNCH(Z, NT)                                                                                    \
+    if (flat) k_backproject<Z, true, NT><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials);    \
+    else k_backproject<Z, false, NT><<<grid, block, smem, st>>>(G, ps, out, isx, isy, isz, out2, partials)
     switch (zc) {
-    case 16: CBCT_BP_LAUNCH(16); break;
-    case 8: CBCT_BP_LAUNCH(8); break;
-    case 4: CBCT_BP_LAUNCH(4); break;
-    case 2: CBCT_BP_LAUNCH(2); break;
-    default: CBCT_BP_LAUNCH(1); break;
+    case 16: CBCT_BP_LAUNCH(16, BP_BIG_THREADS); break;
+    case 8: CBCT_BP_LAUNCH(8, BP_THREADS); break;
+    case 4: CBCT_BP_LAUNCH(4, BP_THREADS); break;
+    case 2: CBCT_BP_LAUNCH(2, BP_THREADS); break;
+    default: CBCT_BP_LAUNCH(1, BP_THREADS); break;
     }
 #undef CBCT_BP_LAUNCH
     prof_stop(tok, st);

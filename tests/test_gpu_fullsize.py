@@ -69,6 +69,13 @@ def test_paper_scale_sampled_parity(cb, level):
     sampled_parity(cb, synth.config_paper(40).level(level), 800 + level)
 
 
+@pytest.mark.parametrize("level", [0, 2])
+def test_paper_scale_80_views_sampled_parity(cb, level):
+    """The workload's second view count (80 views over the turn) on the finest and coarsest
+    grids: twice the table and stack, the same launch shapes per view."""
+    sampled_parity(cb, synth.config_paper(80).level(level), 860 + level)
+
+
 def test_paper_scale_adjoint_identity(cb):
     geom = synth.config_paper(40)
     f = dev(synth.random_volume(geom, 810, 0.0, 0.04))

@@ -11,7 +11,7 @@ The iteration split is reduced to 2/2/2 (coarsest first) so that the oracle fini
 about two minutes on 16 host cores; every launch shape of the benchmark's reconstruction
 runs (each level's P, P^T, fused regularisation step and CGLS updates, and both
 prolongations). Bar: relative L2 <= 1e-3 against the FP64 oracle, for FP32 storage and
-for the BF16 storage of the CGLS residual and projected direction.
+for the BF16 and FP16 storage of the CGLS residual and projected direction.
 
 The same test also checks the library's P of the phantom against the oracle's over the
 whole stack (relative L2 <= 1e-4): the benchmark synthesises its y with the library's P
@@ -79,7 +79,7 @@ def test_paper_projection_of_phantom_matches_oracle(cb, paper_case):
     assert e <= 1e-4, e
 
 
-@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
 def test_paper_reconstruction_matches_oracle(cb, paper_case, storage):
     geom, f_true, _, y, ref = paper_case
     with cb.Geometry(geom) as g:
