@@ -27,12 +27,13 @@ namespace cbct {
 // threads stacks them into a 16 x (NT / 8) tile. Lanes whose columns are close in both x
 // and y read nearby table entries in every view (a voxel's imager column moves with x at
 // some views and with y at others): an 8 x 4 patch touches 10 sectors per table request
-// where a 32 x 1 row touched 16, and the warps of a block share their lines in L1. Blocks
-// of 256 threads (16 x 16 columns) share more of each view's table lines than blocks of
-// 128 and pay where the grid is large (16-voxel chunks: 1.80 -> 1.72 ms for the paper's
-// finest grid); on coarser grids they leave too few blocks, and 128 threads are kept.
+// where a 32 x 1 row touched 16, and the warps of a block share their lines in L1. Larger
+// blocks share more of each view's table lines and pay where the grid is large (16-voxel
+// chunks on the paper's finest grid, kernel alone: 128 threads 1.80 ms, 256 1.72 ms, 512
+// (16 x 32 columns) 1.70 ms, 1024 1.72 ms); on coarser grids they leave too few blocks,
+// and 128 threads are kept.
 constexpr int BP_THREADS = 128;                 // the block size of the coarser grids
-constexpr int BP_BIG_THREADS = 256;             // with 16-voxel chunks
+constexpr int BP_BIG_THREADS = 512;             // with 16-voxel chunks
 constexpr int BP_WX = 8, BP_WY = 4;             // warp patch
 constexpr int BP_BX = 16;                       // block tile along x (two patches)
 template <int NT> constexpr int bp_by() { return BP_WY * (NT / 64); } // block tile along y
