@@ -6,11 +6,14 @@
 // (i2 * n1 + i1) * n0 + i0 with i0 the contiguous axis; channel i = l + 3m + 9n applies
 // h_l along axis 0, h_m along axis 1 and h_n along axis 2. The boundary is periodic.
 //
-// GB300 mapping: a block owns a 32 x 8 tile of the (axis 0, axis 1) plane and marches
-// along axis 2, keeping the planes it needs in shared memory (with a one-voxel halo), so
-// every input value is read from DRAM once and every output written once; warps read
-// and write 128-byte rows along the contiguous axis. Both kernels are bandwidth bound:
-// 4 B in + 108 B out per voxel for W, 108 B in + 4 B out for the shrink/synthesis.
+// GB300 mapping. Every kernel marches along axis 2 so that each input value is read from
+// DRAM once and each output written once, with warps reading and writing rows along the
+// contiguous axis. The analysis W owns a 32 x 8 tile of the (axis 0, axis 1) plane and
+// keeps three planes of it in shared memory (with a one-voxel halo). The shrink +
+// synthesis and the fused step give each lane whole positions and pass neighbour values by
+// warp shuffles (axis 0), a shared exchange (axis 1) and registers (axis 2); they are
+// described at their kernels. The public transforms are bandwidth bound: 4 B in + 108 B
+// out per voxel for W, 108 B in + 4 B out for the shrink/synthesis (FP32 coefficients).
 #include "cbct_internal.cuh"
 
 namespace cbct {
