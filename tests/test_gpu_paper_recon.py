@@ -91,3 +91,19 @@ def test_paper_reconstruction_matches_oracle(cb, paper_case, storage):
     assert out.min() >= 0.0
     # a reconstruction moving toward the phantom from the zero start
     assert rel(ref, f_true) < 1.0
+
+
+def test_paper_reconstruction_80_views_matches_oracle(cb):
+    """The workload's second view count: 80 views, one A2 iteration per level (every level's
+    launch shapes run; the oracle needs about two minutes), FP32, relative L2 <= 1e-3."""
+    geom = synth.config_paper(80)
+    f_true = synth.voxelize(geom, synth.torso_ellipsoids(geom, 1002))
+    y = synth.noisy_line_integrals(oracle.project(geom, f_true), PHOTONS, 2002)
+    iters = [1, 1, 1]
+    ref = oracle.reconstruct(geom, y, MU, LEVELS, iters)
+    with cb.Geometry(geom) as g:
+        out = cb.reconstruct(g, dev(y), MU, LEVELS, iters).cpu().numpy()
+    e = rel(out, ref)
+    print(f"\nreconstruction {geom.nx}x{geom.ny}x{geom.nz}, 80 views, {iters}, f32: relative L2 against the "
+          f"FP64 oracle {e:.2e}")
+    assert e <= 1e-3, e
