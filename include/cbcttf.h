@@ -306,8 +306,9 @@ cbct_status cbct_project_static(const cbct_geometry *geom, const float *f, float
  * run are admitted as soon as slots and memory free up, and their kernels overlap on the
  * device. Two rules keep overlap from costing throughput: the summed volumes of the
  * admitted requests stay within an L2 bound (a request that would break it waits, and
- * smaller requests behind it may start first for a bounded time), and smaller requests
- * run on higher-priority streams.
+ * smaller requests behind it may start first for a bounded time), and stream priorities
+ * order the admitted requests' thread blocks (by size, smallest first, or by age, oldest
+ * first).
  * An admitted request holds one device block (its geometry tables, y, the reconstruction
  * workspace and the output volume) taken from a stream-ordered memory pool; it runs on
  * its slot's stream as: copy y in, the whole multigrid iteration (captured once into a
@@ -318,6 +319,10 @@ cbct_status cbct_project_static(const cbct_geometry *geom, const float *f, float
  */
 typedef struct cbct_server cbct_server;
 
+#define CBCT_PRIORITY_NONE 0
+#define CBCT_PRIORITY_SIZE 1
+#define CBCT_PRIORITY_AGE 2
+
 typedef struct {
     size_t hbm_budget_bytes; /* device bytes admitted requests may hold together; 0 = 150 GB,
                                 capped at 90% of the device memory free at creation */
@@ -327,8 +332,16 @@ typedef struct {
                                 requests, so that the volumes the projectors re-read stay in
                                 L2 together (an idle device always admits); 0 = the device's
                                 L2 size */
-    int size_priority;       /* 1 = requests get stream priority by volume size, smallest
-                                first (their thread blocks are scheduled ahead) */
+    int size_priority;       /* stream priorities (a request's thread blocks are scheduled
+                                ahead of those of lower-priority requests):
+                                CBCT_PRIORITY_NONE (0) = all equal;
+                                CBCT_PRIORITY_SIZE (1) = by volume size, smallest first;
+                                CBCT_PRIORITY_AGE (2) = by admission order, oldest first:
+                                the oldest request runs as if alone and the others fill
+                                what it leaves idle; a request moves up as older ones
+                                finish (its iteration is enqueued one A2 iteration at a
+                                time, each on the streams of its current rank; use_graphs
+                                is ignored) */
     double max_bypass_s;     /* a queued request held back by the L2 bound is overtaken by
                                 later requests only until it has waited this long; 0 = 2 s */
 } cbct_server_opts;

@@ -497,11 +497,20 @@ class Server:
     host buffers and returns at once; wait() blocks until it is done. Requests run
     concurrently on the GPU, admitted by slots and by the device-memory budget."""
 
+    PRIORITIES = {"none": 0, "size": 1, "age": 2}
+
     def __init__(self, budget_bytes: int = 0, max_active: int = 16, use_graphs: bool = True,
-                 l2_budget_bytes: int = 0, size_priority: bool = True, max_bypass_s: float = 0.0):
+                 l2_budget_bytes: int = 0, size_priority: bool = True, max_bypass_s: float = 0.0,
+                 priority: Optional[str] = None):
+        """priority: "size" (smallest requests first), "age" (oldest first, re-ranked after
+        every A2 iteration) or "none"; None takes "size" or "none" from size_priority."""
         lib = load_library()
+        if priority is None:
+            priority = "size" if size_priority else "none"
+        if priority not in self.PRIORITIES:
+            raise ValueError(f"priority must be one of {sorted(self.PRIORITIES)}")
         o = ServerOpts(int(budget_bytes), int(max_active), int(bool(use_graphs)), int(l2_budget_bytes),
-                       int(bool(size_priority)), float(max_bypass_s))
+                       self.PRIORITIES[priority], float(max_bypass_s))
         h = ctypes.c_void_p()
         _check(lib.cbct_server_create(ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -9,6 +9,9 @@
 // the host.
 #include <cmath>
 #include <cstring>
+#include <memory>
+#include <utility>
+#include <vector>
 
 #include "cbct_internal.cuh"
 
@@ -449,6 +452,7 @@ static cbct_status read_flags(const Work &w, cudaStream_t st)
     cudaError_t e = cudaMemcpyAsync(&flags, &w.sc->flags, sizeof(flags), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return check_cuda(e, "status read-back");
+    if (flags & 2u) return set_error(CBCT_ERR_TIMEOUT, "a projector block timed out waiting for its staged volume lines");
     if (flags & 1u) return set_error(CBCT_ERR_NONFINITE, "an inner product of the iteration was not finite");
     return CBCT_OK;
 }
@@ -462,59 +466,128 @@ static cbct_status reset_scalars(const Work &w, cudaStream_t st)
 // Algorithm A2 on one level and the multigrid driver
 // ------------------------------------------------------------------------------------
 
-static cbct_status run_a2(const GeomDev &G, const float *y, float mu, int iters, const cbct_recon_opts &o,
-                          Work &w, float **f_cur, float **f_other, cudaStream_t st)
+// One iteration k of Algorithm A2 on one level: CGLS from the momentum point X, then
+// f^(k+1) = H(D^T T_mu D x) fused with the next momentum point
+// v^(k+1) = f^(k+1) + (t^(k) - 1) / t^(k+1) (f^(k+1) - f^(k)) into X2 (skipped on the
+// level's last iteration); t is advanced to t^(k+1). Internal layout: axis 0 = z,
+// axis 1 = x, axis 2 = y.
+static cbct_status run_a2_iteration(const GeomDev &G, const float *y, float mu, bool last, const cbct_recon_opts &o,
+                                    Work &w, double &t, float **f_cur, float **f_other, cudaStream_t st)
 {
-    const size_t N = (size_t)G.nx * G.ny * G.nz;
-    // v^(0) = f^(0): the first momentum coefficient is 0
-    TRY(check_cuda(cudaMemcpyAsync(w.X, *f_cur, sizeof(float) * N, cudaMemcpyDeviceToDevice, st), "copy"));
-    double t = 1.0; // t^(k)
-    for (int k = 0; k < iters; ++k) {
-        TRY(run_cgls(G, y, w.X, o.n_cgls, w, o.storage, st));
-        // f^(k+1) = H(D^T T_mu D x) fused with the next momentum point
-        // v^(k+1) = f^(k+1) + (t^(k) - 1) / t^(k+1) (f^(k+1) - f^(k)) into X2;
-        // internal layout: axis 0 = z, axis 1 = x, axis 2 = y
-        const double t_next = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
-        const bool last = k + 1 == iters;
-        const float c = o.momentum ? (float)((t - 1.0) / t_next) : 0.0f;
-        TRY(launch_tf_shrink_fused(G.nz, G.nx, G.ny, w.X, mu, o.positivity, *f_other, *f_cur, c,
-                                   last ? nullptr : w.X2, st));
-        float *tmp = *f_cur;
-        *f_cur = *f_other;
-        *f_other = tmp;
-        tmp = w.X;
-        w.X = w.X2;
-        w.X2 = tmp;
-        t = t_next;
-    }
+    TRY(run_cgls(G, y, w.X, o.n_cgls, w, o.storage, st));
+    const double t_next = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+    const float c = o.momentum ? (float)((t - 1.0) / t_next) : 0.0f;
+    TRY(launch_tf_shrink_fused(G.nz, G.nx, G.ny, w.X, mu, o.positivity, *f_other, *f_cur, c, last ? nullptr : w.X2,
+                               st));
+    std::swap(*f_cur, *f_other);
+    std::swap(w.X, w.X2);
+    t = t_next;
     return CBCT_OK;
+}
+
+// A reconstruction as a sequence of steps, each one A2 iteration of one level; a level's
+// set-up (the zero start on the coarsest grid, the prolongation onto the next) rides on
+// its first step and the change back to the public layout on the last. Enqueued step by
+// step, on one stream or handed from stream to stream, it issues exactly the launches of
+// the whole-run enqueue below (which is this loop), so the results are bit-identical.
+struct ReconCursor {
+    const float *y = nullptr;
+    cbct_geometry *g = nullptr;
+    float mu = 0.0f;
+    int levels = 1;
+    std::vector<int> iters;
+    cbct_recon_opts o{};
+    float *f_out = nullptr;
+    Work w{};
+    bool started = false, finished = false, need_setup = true;
+    int lev = 0, k = 0;  // current level (levels - 1 = coarsest) and its next A2 iteration
+    double t = 1.0;      // t^(k) of Algorithm A2 on the current level
+    float *f_cur = nullptr, *f_other = nullptr;
+    GeomDev Gprev{};
+};
+
+cbct_status reconstruct_cursor_create(const float *y, cbct_geometry *g, float mu, int levels, const int *iters,
+                                      const cbct_recon_opts &o, void *ws, size_t ws_bytes, float *f_out,
+                                      ReconCursor **out)
+{
+    std::unique_ptr<ReconCursor> c(new ReconCursor());
+    TRY(get_work(g, ws, ws_bytes, &c->w));
+    c->y = y;
+    c->g = g;
+    c->mu = mu;
+    c->levels = levels;
+    c->iters.assign(iters, iters + levels);
+    c->o = o;
+    c->f_out = f_out;
+    *out = c.release();
+    return CBCT_OK;
+}
+
+void reconstruct_cursor_destroy(ReconCursor *c) { delete c; }
+
+bool reconstruct_cursor_finished(const ReconCursor *c) { return c->finished; }
+
+cbct_status reconstruct_cursor_step(ReconCursor *c, cudaStream_t st)
+{
+    if (c->finished) return CBCT_OK;
+    Work &w = c->w;
+    if (!c->started) {
+        TRY(reset_scalars(w, st));
+        c->f_cur = w.Fa;
+        c->f_other = w.Fb;
+        c->lev = c->levels - 1;
+        c->k = 0;
+        c->need_setup = true;
+        c->started = true;
+    }
+    for (;;) {
+        if (c->lev < 0) { // every level done: the volume back to the public layout
+            const GeomDev G0 = level_geom(c->g, 0);
+            TRY(transpose(c->f_cur, c->f_out, G0.nx, G0.ny, G0.nz, false, st));
+            c->finished = true;
+            return CBCT_OK;
+        }
+        const GeomDev G = level_geom(c->g, c->lev);
+        const size_t N = (size_t)G.nx * G.ny * G.nz;
+        const int iters = c->iters[c->levels - 1 - c->lev];
+        if (c->need_setup) {
+            if (c->lev == c->levels - 1) {
+                TRY(check_cuda(cudaMemsetAsync(c->f_cur, 0, sizeof(float) * N, st), "memset"));
+            } else {
+                const GeomDev &P = c->Gprev;
+                TRY(launch_prolong(grid3(P.nx, P.ny, P.nz, P.dx, P.dy, P.dz), c->f_cur,
+                                   grid3(G.nx, G.ny, G.nz, G.dx, G.dy, G.dz), c->f_other, 1, st));
+                std::swap(c->f_cur, c->f_other);
+            }
+            // v^(0) = f^(0): the first momentum coefficient is 0
+            TRY(check_cuda(cudaMemcpyAsync(w.X, c->f_cur, sizeof(float) * N, cudaMemcpyDeviceToDevice, st), "copy"));
+            c->t = 1.0;
+            c->need_setup = false;
+        }
+        const bool had_iteration = c->k < iters;
+        if (had_iteration) {
+            TRY(run_a2_iteration(G, c->y, c->mu, c->k + 1 == iters, c->o, w, c->t, &c->f_cur, &c->f_other, st));
+            c->k++;
+        }
+        if (c->k >= iters) { // level done: the next one starts with the prolongation
+            c->Gprev = G;
+            c->lev--;
+            c->k = 0;
+            c->need_setup = true;
+            if (c->lev < 0) continue; // the final layout change belongs to this step
+        }
+        if (had_iteration) return CBCT_OK;
+    }
 }
 
 cbct_status reconstruct_enqueue(const float *y, cbct_geometry *g, float mu, int levels, const int *iters,
                                 const cbct_recon_opts &o, void *ws, size_t ws_bytes, float *f_out, cudaStream_t st)
 {
-    Work w;
-    TRY(get_work(g, ws, ws_bytes, &w));
-    TRY(reset_scalars(w, st));
-    float *f_cur = w.Fa, *f_other = w.Fb;
-    GeomDev Gprev{};
-    for (int lev = levels - 1; lev >= 0; --lev) {
-        const GeomDev G = level_geom(g, lev);
-        const size_t N = (size_t)G.nx * G.ny * G.nz;
-        if (lev == levels - 1) {
-            TRY(check_cuda(cudaMemsetAsync(f_cur, 0, sizeof(float) * N, st), "memset"));
-        } else {
-            TRY(launch_prolong(grid3(Gprev.nx, Gprev.ny, Gprev.nz, Gprev.dx, Gprev.dy, Gprev.dz), f_cur,
-                               grid3(G.nx, G.ny, G.nz, G.dx, G.dy, G.dz), f_other, 1, st));
-            float *tmp = f_cur;
-            f_cur = f_other;
-            f_other = tmp;
-        }
-        TRY(run_a2(G, y, mu, iters[levels - 1 - lev], o, w, &f_cur, &f_other, st));
-        Gprev = G;
-    }
-    const GeomDev G0 = level_geom(g, 0);
-    return transpose(f_cur, f_out, G0.nx, G0.ny, G0.nz, false, st);
+    ReconCursor *c = nullptr;
+    TRY(reconstruct_cursor_create(y, g, mu, levels, iters, o, ws, ws_bytes, f_out, &c));
+    std::unique_ptr<ReconCursor> hold(c);
+    while (!c->finished) TRY(reconstruct_cursor_step(c, st));
+    return CBCT_OK;
 }
 
 size_t reconstruct_ws_bytes(const cbct_geometry *g) { return work_layout(g, nullptr, nullptr); }

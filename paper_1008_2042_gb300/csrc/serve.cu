@@ -9,12 +9,23 @@
 // requests to finish their work: new requests join while earlier ones are mid-iteration,
 // and the GPU runs the kernels of all active streams side by side.
 //
+// Priorities. Under size priority a request's whole pipeline goes to a stream of its
+// size class, smallest first. Under age priority the oldest admitted request runs on the
+// highest-priority streams, the next oldest one level lower, and so on: the request at
+// the head of the line keeps the GPU almost as if it ran alone (its thread blocks are
+// scheduled first), and the others fill what it leaves idle (kernel tails, small
+// launches, the gaps between dependent launches). Requests move up as older ones finish,
+// so their work is enqueued step by step (one A2 iteration per step, at most three steps
+// in flight), each step on the stream of the request's current rank and ordered after
+// the previous step by an event.
+//
 // Device memory: every request takes one block from a stream-ordered pool
 // (cudaMallocFromPoolAsync on its stream) and gives it back with cudaFreeAsync after its
 // last copy, so blocks are reused across requests without device-wide synchronisation.
 // Each block holds the request's geometry tables, y, the reconstruction workspace and
 // the output volume; nothing is shared between requests, and every kernel of the
 // iteration is deterministic, so a request's result does not depend on its neighbours.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -37,6 +48,8 @@ constexpr int DEFAULT_SLOTS = 16;
 constexpr int MAX_SLOTS = 64;
 constexpr double DEFAULT_BYPASS_S = 2.0;
 constexpr int N_CLASSES = 3; // stream priority classes: small, medium, large requests
+constexpr int MAX_AGE_LEVELS = 8; // priority levels used under age priority (capped by the device's range)
+constexpr int STEPS_AHEAD = 3;    // age priority: steps of one request in flight at once
 
 enum RequestState { RQ_QUEUED = 0, RQ_ACTIVE = 1, RQ_DONE = 2 };
 
@@ -61,6 +74,12 @@ struct Request {
     char *block = nullptr;
     cudaEvent_t done_ev = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // age priority: the reconstruction enqueued step by step
+    ReconCursor *cursor = nullptr;
+    cudaEvent_t step_ev[STEPS_AHEAD] = {};        // the last steps issued (ring)
+    long long steps_issued = 0, steps_done = 0;  // the set-up copies count as step 0
+    int cur_stream = -1;                         // stream index of the last step
+    bool tail_enqueued = false;                  // the copy-out and release are enqueued
     RequestState state = RQ_QUEUED;
     cbct_status status = CBCT_OK;
     std::string message;
@@ -79,8 +98,9 @@ struct cbct_server {
     cudaMemPool_t pool = nullptr;
     size_t l2_budget = 0;               // bound on the summed wset of admitted requests
     double max_bypass_s = DEFAULT_BYPASS_S;
-    std::vector<cudaStream_t> streams;  // N_CLASSES x max_active, class-major
-    std::vector<int> free_slots[N_CLASSES];
+    int nclass = N_CLASSES;             // priority levels (stream classes)
+    std::vector<cudaStream_t> streams;  // nclass x max_active, class-major
+    std::vector<int> free_slots[N_CLASSES]; // size/none: stream indices per class; age: slots in [0]
     unsigned int *flags_host = nullptr; // one pinned status word per stream (64-byte stride)
     std::mutex mu;
     std::condition_variable cv_done, cv_work;
@@ -97,6 +117,8 @@ struct cbct_server {
 
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
     unsigned int *slot_flags(int slot) { return flags_host + 16 * slot; }
+    bool age() const { return opts.size_priority == CBCT_PRIORITY_AGE; }
+    cudaStream_t stream_of(int cls, int slot) const { return streams[(size_t)cls * opts.max_active + slot]; }
 };
 
 namespace {
@@ -139,10 +161,10 @@ bool is_pinned(const void *p)
         if (_s != CBCT_OK) return _s;                                                              \
     } while (0)
 
-// Enqueues everything a request does on its slot's stream. Runs on the worker thread.
-cbct_status enqueue_request(cbct_server *srv, Request *r)
+// The set-up of a request on stream st: its device block, the view and ray tables and
+// the projections. Runs on the worker thread.
+cbct_status enqueue_prologue(cbct_server *srv, Request *r, cudaStream_t st)
 {
-    cudaStream_t st = srv->streams[r->slot];
     void *blk = nullptr;
     SRV_TRY(check_cuda(cudaMallocFromPoolAsync(&blk, r->bytes, srv->pool, st), "server: device block"));
     r->block = (char *)blk;
@@ -150,17 +172,44 @@ cbct_status enqueue_request(cbct_server *srv, Request *r)
     g.d_cs = reinterpret_cast<float2 *>(r->block + r->off_cs);
     g.d_ray4 = reinterpret_cast<float4 *>(r->block + r->off_ray4);
     g.d_ray2 = reinterpret_cast<float2 *>(r->block + r->off_ray2);
-    float *y_dev = reinterpret_cast<float *>(r->block + r->off_y);
-    float *f_dev = reinterpret_cast<float *>(r->block + r->off_f);
-    void *ws = r->block + r->off_ws;
     const cbct_geometry_desc &d = g.desc;
-    const size_t M = (size_t)d.n_views * d.nv * d.nu, N = (size_t)d.nx * d.ny * d.nz;
-
+    const size_t M = (size_t)d.n_views * d.nv * d.nu;
     SRV_TRY(check_cuda(cudaMemcpyAsync(g.d_cs, r->cs.data(), sizeof(float2) * d.n_views, cudaMemcpyHostToDevice, st),
                        "server: view table"));
     SRV_TRY(launch_ray_table(&g, st));
-    SRV_TRY(check_cuda(cudaMemcpyAsync(y_dev, r->y_host, sizeof(float) * M, cudaMemcpyHostToDevice, st),
-                       "server: projections in"));
+    return check_cuda(cudaMemcpyAsync(r->block + r->off_y, r->y_host, sizeof(float) * M, cudaMemcpyHostToDevice, st),
+                      "server: projections in");
+}
+
+// The end of a request on stream st: the volume and the status word out, the block back
+// to the pool once the copies have run, then the completion event (so a retired
+// request's bytes are free in the pool as well as in the budget).
+cbct_status enqueue_tail(cbct_server *srv, Request *r, cudaStream_t st)
+{
+    const cbct_geometry_desc &d = r->geom.desc;
+    const size_t N = (size_t)d.nx * d.ny * d.nz;
+    SRV_TRY(check_cuda(cudaMemcpyAsync(r->f_host, r->block + r->off_f, sizeof(float) * N, cudaMemcpyDeviceToHost, st),
+                       "server: volume out"));
+    SRV_TRY(check_cuda(cudaMemcpyAsync(srv->slot_flags(r->slot), reconstruct_flags_address(&r->geom, r->block + r->off_ws),
+                                       sizeof(unsigned int), cudaMemcpyDeviceToHost, st),
+                       "server: status out"));
+    cudaError_t e = cudaFreeAsync(r->block, st);
+    if (e != cudaSuccess) return check_cuda(e, "server: block release");
+    r->block = nullptr;
+    SRV_TRY(check_cuda(cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming), "server: event"));
+    return check_cuda(cudaEventRecord(r->done_ev, st), "server: event");
+}
+
+// Enqueues everything a request does on its slot's stream (size or no priority). Runs on
+// the worker thread.
+cbct_status enqueue_request(cbct_server *srv, Request *r)
+{
+    cudaStream_t st = srv->streams[r->slot];
+    SRV_TRY(enqueue_prologue(srv, r, st));
+    cbct_geometry &g = r->geom;
+    const float *y_dev = reinterpret_cast<const float *>(r->block + r->off_y);
+    float *f_dev = reinterpret_cast<float *>(r->block + r->off_f);
+    void *ws = r->block + r->off_ws;
     if (srv->opts.use_graphs) {
         SRV_TRY(check_cuda(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "server: capture"));
         cbct_status s = reconstruct_enqueue(y_dev, &g, r->mu, r->levels, r->iters.data(), r->opts, ws, r->ws_bytes,
@@ -182,18 +231,73 @@ cbct_status enqueue_request(cbct_server *srv, Request *r)
     } else {
         SRV_TRY(reconstruct_enqueue(y_dev, &g, r->mu, r->levels, r->iters.data(), r->opts, ws, r->ws_bytes, f_dev, st));
     }
-    SRV_TRY(check_cuda(cudaMemcpyAsync(r->f_host, f_dev, sizeof(float) * N, cudaMemcpyDeviceToHost, st),
-                       "server: volume out"));
-    SRV_TRY(check_cuda(cudaMemcpyAsync(srv->slot_flags(r->slot), reconstruct_flags_address(&g, ws),
-                                       sizeof(unsigned int), cudaMemcpyDeviceToHost, st),
-                       "server: status out"));
-    // back to the pool once the copies have run; the completion event follows the release,
-    // so a retired request's bytes are free in the pool as well as in the budget
-    cudaError_t e = cudaFreeAsync(r->block, st);
-    if (e != cudaSuccess) return check_cuda(e, "server: block release");
-    r->block = nullptr;
-    SRV_TRY(check_cuda(cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming), "server: event"));
-    return check_cuda(cudaEventRecord(r->done_ev, st), "server: event");
+    return enqueue_tail(srv, r, st);
+}
+
+// Age priority: the set-up of a newly admitted request on the streams of priority level
+// cls; its steps follow from issue_steps.
+cbct_status enqueue_request_stepped(cbct_server *srv, Request *r, int cls)
+{
+    const int idx = cls * srv->opts.max_active + r->slot;
+    cudaStream_t st = srv->streams[idx];
+    for (cudaEvent_t &ev : r->step_ev)
+        SRV_TRY(check_cuda(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "server: event"));
+    SRV_TRY(enqueue_prologue(srv, r, st));
+    SRV_TRY(reconstruct_cursor_create(reinterpret_cast<const float *>(r->block + r->off_y), &r->geom, r->mu, r->levels,
+                                      r->iters.data(), r->opts, r->block + r->off_ws, r->ws_bytes,
+                                      reinterpret_cast<float *>(r->block + r->off_f), &r->cursor));
+    SRV_TRY(check_cuda(cudaEventRecord(r->step_ev[0], st), "server: event"));
+    r->steps_issued = 1;
+    r->cur_stream = idx;
+    return CBCT_OK;
+}
+
+// Age priority: notes the request's finished steps and keeps STEPS_AHEAD in flight, the new ones
+// on the streams of priority level cls (ordered after the previous step by its event);
+// after the last step, the tail. Runs on the worker thread without the lock.
+cbct_status issue_steps(cbct_server *srv, Request *r, int cls, bool &progressed)
+{
+    while (r->steps_done < r->steps_issued) {
+        const cudaError_t e = cudaEventQuery(r->step_ev[r->steps_done % STEPS_AHEAD]);
+        if (e == cudaErrorNotReady) break;
+        if (e != cudaSuccess) return check_cuda(e, "server: request work");
+        r->steps_done++;
+    }
+    const int idx = cls * srv->opts.max_active + r->slot;
+    while (!r->tail_enqueued && r->steps_issued - r->steps_done < STEPS_AHEAD) {
+        cudaStream_t st = srv->streams[idx];
+        if (idx != r->cur_stream)
+            SRV_TRY(check_cuda(cudaStreamWaitEvent(st, r->step_ev[(r->steps_issued - 1) % STEPS_AHEAD], 0),
+                               "server: step order"));
+        r->cur_stream = idx;
+        SRV_TRY(reconstruct_cursor_step(r->cursor, st));
+        progressed = true;
+        if (reconstruct_cursor_finished(r->cursor)) {
+            SRV_TRY(enqueue_tail(srv, r, st));
+            r->tail_enqueued = true;
+        } else {
+            // step steps_issued - STEPS_AHEAD, the previous user of this event, has completed
+            SRV_TRY(check_cuda(cudaEventRecord(r->step_ev[r->steps_issued % STEPS_AHEAD], st), "server: event"));
+            r->steps_issued++;
+        }
+    }
+    return CBCT_OK;
+}
+
+// Leaves a failed request's streams idle and its block back in the pool. Runs without
+// the lock.
+void abort_request(cbct_server *srv, Request *r)
+{
+    const int ncls = srv->age() ? srv->nclass : 1;
+    for (int c = 0; c < ncls; ++c)
+        cudaStreamSynchronize(srv->age() ? srv->stream_of(c, r->slot) : srv->streams[r->slot]);
+    if (r->block) {
+        cudaStream_t st = srv->age() ? srv->stream_of(0, r->slot) : srv->streams[r->slot];
+        cudaFreeAsync(r->block, st);
+        cudaStreamSynchronize(st);
+        r->block = nullptr;
+    }
+    cudaGetLastError();
 }
 
 // Returns a request's slot and bytes. Caller holds the lock.
@@ -206,6 +310,15 @@ void retire(cbct_server *srv, Request *r, cbct_status status, const std::string 
     if (r->done_ev) {
         cudaEventDestroy(r->done_ev);
         r->done_ev = nullptr;
+    }
+    for (cudaEvent_t &ev : r->step_ev)
+        if (ev) {
+            cudaEventDestroy(ev);
+            ev = nullptr;
+        }
+    if (r->cursor) {
+        reconstruct_cursor_destroy(r->cursor);
+        r->cursor = nullptr;
     }
     r->status = status;
     r->message = msg;
@@ -228,6 +341,10 @@ void worker_main(cbct_server *srv)
         // 1. retire requests whose work has completed
         for (size_t i = 0; i < srv->active.size();) {
             Request *r = srv->active[i];
+            if (!r->done_ev) { // age priority: still being enqueued step by step
+                ++i;
+                continue;
+            }
             cudaError_t e = cudaEventQuery(r->done_ev);
             if (e == cudaErrorNotReady) {
                 ++i;
@@ -238,6 +355,9 @@ void worker_main(cbct_server *srv)
             if (e != cudaSuccess) {
                 status = check_cuda(e, "server: request work");
                 msg = cbct_last_error();
+            } else if (*srv->slot_flags(r->slot) & 2u) {
+                status = CBCT_ERR_TIMEOUT;
+                msg = "a projector block timed out waiting for its staged volume lines";
             } else if (*srv->slot_flags(r->slot) & 1u) {
                 status = CBCT_ERR_NONFINITE;
                 msg = "an inner product of the iteration was not finite";
@@ -246,6 +366,33 @@ void worker_main(cbct_server *srv)
             srv->active[i] = srv->active.back();
             srv->active.pop_back();
             progressed = true;
+        }
+        // 1b. age priority: steps of the admitted requests, oldest first, each on the
+        //     streams of its rank (the oldest on the highest priority)
+        if (srv->age() && !srv->active.empty()) {
+            std::vector<Request *> order(srv->active);
+            std::sort(order.begin(), order.end(), [](const Request *a, const Request *b) { return a->id < b->id; });
+            std::vector<std::pair<Request *, cbct_status>> failed;
+            std::vector<std::string> messages;
+            lk.unlock(); // only this thread changes the admitted requests
+            for (size_t rank = 0; rank < order.size(); ++rank) {
+                Request *r = order[rank];
+                if (r->tail_enqueued) continue;
+                const int cls = (int)std::min<size_t>(rank, (size_t)srv->nclass - 1);
+                const cbct_status st = issue_steps(srv, r, cls, progressed);
+                if (st != CBCT_OK) {
+                    failed.emplace_back(r, st);
+                    messages.emplace_back(cbct_last_error());
+                    abort_request(srv, r);
+                }
+            }
+            lk.lock();
+            for (size_t f = 0; f < failed.size(); ++f) {
+                Request *r = failed[f].first;
+                srv->active.erase(std::find(srv->active.begin(), srv->active.end(), r));
+                retire(srv, r, failed[f].second, messages[f]);
+                progressed = true;
+            }
         }
         // 2. admission. Scan the queue in submission order while a slot is free. Device
         //    memory is granted strictly in order (the scan stops at the first request the
@@ -264,6 +411,7 @@ void worker_main(cbct_server *srv)
             }
             if (it != srv->queue.begin()) srv->bypassed++;
             it = srv->queue.erase(it);
+            if (srv->age()) r->cls = 0; // one list of slots; the priority level follows the rank
             r->slot = srv->free_slots[r->cls].back();
             srv->free_slots[r->cls].pop_back();
             r->state = RQ_ACTIVE;
@@ -273,19 +421,13 @@ void worker_main(cbct_server *srv)
             if (srv->bytes_in_use > srv->max_bytes_seen) srv->max_bytes_seen = srv->bytes_in_use;
             srv->active.push_back(r); // listed before the unlock: retire() runs only under the lock
             if ((int)srv->active.size() > srv->max_active_seen) srv->max_active_seen = (int)srv->active.size();
+            // the newest admitted request is the youngest: the lowest rank so far
+            const int cls_age = std::min((int)srv->active.size() - 1, srv->nclass - 1);
             lk.unlock();
-            cbct_status s = enqueue_request(srv, r);
+            cbct_status s = srv->age() ? enqueue_request_stepped(srv, r, cls_age) : enqueue_request(srv, r);
             std::string msg = s == CBCT_OK ? std::string() : std::string(cbct_last_error());
-            if (s != CBCT_OK) {
-                // leave the stream idle and the block back in the pool before the slot is reused
-                cudaStreamSynchronize(srv->streams[r->slot]);
-                if (r->block) {
-                    cudaFreeAsync(r->block, srv->streams[r->slot]);
-                    cudaStreamSynchronize(srv->streams[r->slot]);
-                    r->block = nullptr;
-                }
-                cudaGetLastError();
-            }
+            // leave the streams idle and the block back in the pool before the slot is reused
+            if (s != CBCT_OK) abort_request(srv, r);
             lk.lock();
             if (s != CBCT_OK) {
                 for (size_t i = 0; i < srv->active.size(); ++i)
@@ -333,8 +475,13 @@ extern "C" cbct_status cbct_server_create(const cbct_server_opts *opts, cbct_ser
     SRV_TRY(check_cuda(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, srv->device), "server_create"));
     srv->l2_budget = o.l2_budget_bytes ? o.l2_budget_bytes : (size_t)l2;
     srv->max_bypass_s = o.max_bypass_s > 0.0 ? o.max_bypass_s : DEFAULT_BYPASS_S;
+    if (o.size_priority < CBCT_PRIORITY_NONE || o.size_priority > CBCT_PRIORITY_AGE)
+        return set_error(CBCT_ERR_INVALID_ARG, "server_create: size_priority must be 0 (none), 1 (size) or 2 (age)");
     int least = 0, greatest = 0;
     SRV_TRY(check_cuda(cudaDeviceGetStreamPriorityRange(&least, &greatest), "server_create"));
+    // age priority: one level per rank, as many as the device offers (up to MAX_AGE_LEVELS)
+    srv->nclass = o.size_priority == CBCT_PRIORITY_AGE ? std::max(1, std::min(MAX_AGE_LEVELS, least - greatest + 1))
+                                                       : N_CLASSES;
     // kernels' shared-memory opt-ins, so that nothing is set while a stream is captured
     SRV_TRY(project_prepare());
     SRV_TRY(tf_prepare());
@@ -346,15 +493,19 @@ extern "C" cbct_status cbct_server_create(const cbct_server_opts *opts, cbct_ser
     SRV_TRY(check_cuda(cudaMemPoolCreate(&srv->pool, &props), "server_create: memory pool"));
     unsigned long long keep = ~0ull; // keep freed blocks in the pool for the next requests
     cudaMemPoolSetAttribute(srv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
-    const int nstreams = N_CLASSES * o.max_active;
+    const int nstreams = srv->nclass * o.max_active;
     cudaError_t e = cudaHostAlloc(&srv->flags_host, sizeof(unsigned int) * 16 * nstreams, cudaHostAllocDefault);
     if (e != cudaSuccess) {
         cudaMemPoolDestroy(srv->pool);
         return check_cuda(e, "server_create: status words");
     }
-    for (int c = 0; c < N_CLASSES; ++c) {
-        // class 0 (small requests) gets the greatest priority, the last class the least
-        const int prio = !o.size_priority ? 0 : c == 0 ? greatest : c == N_CLASSES - 1 ? least : (greatest + least) / 2;
+    for (int c = 0; c < srv->nclass; ++c) {
+        // size: class 0 (small requests) gets the greatest priority, the last class the
+        // least; age: level c (rank c, 0 = oldest) gets the c-th greatest
+        const int prio = o.size_priority == CBCT_PRIORITY_AGE ? greatest + c
+                         : o.size_priority == CBCT_PRIORITY_SIZE
+                             ? (c == 0 ? greatest : c == N_CLASSES - 1 ? least : (greatest + least) / 2)
+                             : 0;
         for (int s = 0; s < o.max_active; ++s) {
             cudaStream_t st;
             e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio);
@@ -364,7 +515,8 @@ extern "C" cbct_status cbct_server_create(const cbct_server_opts *opts, cbct_ser
                 cudaMemPoolDestroy(srv->pool);
                 return check_cuda(e, "server_create: streams");
             }
-            srv->free_slots[c].push_back((int)srv->streams.size());
+            if (o.size_priority != CBCT_PRIORITY_AGE) srv->free_slots[c].push_back((int)srv->streams.size());
+            else if (c == 0) srv->free_slots[0].push_back(s);
             srv->streams.push_back(st);
         }
     }

@@ -14,7 +14,9 @@ Two arms over the same request list:
 * plain: FP32 CGLS vectors, one request on the device at a time, no graphs;
 * served: BF16 CGLS vectors, up to 16 requests on the device, each captured as a CUDA graph,
   admitted under the L2 bound, smaller requests on higher-priority streams (also run
-  without the priorities, Poisson arrivals only, to show what they trade).
+  without the priorities, Poisson arrivals only, to show what they trade);
+* served by age: the same, with the oldest admitted request on the highest-priority
+  streams and the others filling what it leaves idle, re-ranked after every A2 iteration.
 Each arm runs twice: all requests submitted at once (throughput: requests per second of
 makespan) and with Poisson arrivals at a fraction of the plain arm's measured capacity
 (latency: p50 / p99 of completion minus submission). Every served volume is compared with
@@ -87,11 +89,11 @@ def prepare_inputs(cb, trace, device="cuda"):
     return ys
 
 
-def run_arm(cb, trace, ys, outs, *, storage, max_active, use_graphs, rate=None, size_priority=True):
+def run_arm(cb, trace, ys, outs, *, storage, max_active, use_graphs, rate=None, priority="size"):
     """Submits every request (all at once when rate is None, else at its arrival time on
     a Poisson clock of `rate` requests per second) and waits for all. Returns makespan and
     per-request latencies (seconds, server clock)."""
-    with cb.Server(max_active=max_active, use_graphs=use_graphs, size_priority=size_priority) as srv:
+    with cb.Server(max_active=max_active, use_graphs=use_graphs, priority=priority) as srv:
         t_start = time.perf_counter()
         ids = []
         for r, y, o in zip(trace, ys, outs):
@@ -136,6 +138,7 @@ def main(argv=None):
     wo = [torch.empty_like(out_plain[trace.index(r)]).pin_memory() for r in warm]
     run_arm(cb, warm, wy, wo, storage="f32", max_active=1, use_graphs=False)
     run_arm(cb, warm, wy, wo, storage="bf16", max_active=args.max_active, use_graphs=True)
+    run_arm(cb, warm, wy, wo, storage="bf16", max_active=args.max_active, use_graphs=False, priority="age")
 
     plain_sat = run_arm(cb, trace, ys, out_plain, storage="f32", max_active=1, use_graphs=False)
     served_sat = run_arm(cb, trace, ys, out_served, storage="bf16", max_active=args.max_active, use_graphs=True)
@@ -146,7 +149,14 @@ def main(argv=None):
     served_open = run_arm(cb, trace, ys, out_served, storage="bf16", max_active=args.max_active, use_graphs=True,
                           rate=rate)
     served_open_flat = run_arm(cb, trace, ys, out_served, storage="bf16", max_active=args.max_active,
-                               use_graphs=True, rate=rate, size_priority=False)
+                               use_graphs=True, rate=rate, priority="none")
+    out_age = [torch.empty_like(o).pin_memory() for o in out_plain]
+    age_sat = run_arm(cb, trace, ys, out_age, storage="bf16", max_active=args.max_active, use_graphs=False,
+                      priority="age")
+    age_open = run_arm(cb, trace, ys, out_age, storage="bf16", max_active=args.max_active, use_graphs=False,
+                       rate=rate, priority="age")
+    errs_age = [float(np.linalg.norm(a.numpy().astype(np.float64) - s.numpy()) / max(np.linalg.norm(s.numpy()), 1e-30))
+                for a, s in zip(out_age, out_served)]
     counts = {s: sum(r["shape"] == s for r in trace) for s in SHAPES}
     line = {
         "metric": "served reconstructions per second and latency",
@@ -156,6 +166,9 @@ def main(argv=None):
         "plain_f32_one_at_a_time": {"all_at_once": plain_sat, "poisson": plain_open},
         "served_bf16_concurrent": {"all_at_once": served_sat, "poisson": served_open,
                                    "poisson_without_size_priority": served_open_flat},
+        "served_bf16_age_priority": {"all_at_once": age_sat, "poisson": age_open,
+                                     "rel_l2_vs_size_priority_max": max(errs_age)},
+        "throughput_ratio_age_vs_plain": age_sat["recon_per_s"] / plain_sat["recon_per_s"],
         "poisson_rate_per_s": rate, "load_vs_plain_capacity": args.load,
         "throughput_ratio_served_vs_plain": served_sat["recon_per_s"] / plain_sat["recon_per_s"],
         "rel_l2_served_bf16_vs_plain_f32": {"max": max(errs), "median": percentile(errs, 50)},

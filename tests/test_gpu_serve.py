@@ -76,9 +76,11 @@ def alone(cb, mix_inputs):
     return outs
 
 
-@pytest.mark.parametrize("use_graphs", [True, False])
-def test_results_are_the_same_alone_and_in_the_mix(cb, mix_inputs, alone, use_graphs):
-    with cb.Server(max_active=4, use_graphs=use_graphs) as srv:
+@pytest.mark.parametrize("use_graphs,priority", [(True, "size"), (False, "size"), (True, "age"), (False, "none")])
+def test_results_are_the_same_alone_and_in_the_mix(cb, mix_inputs, alone, use_graphs, priority):
+    """Under age priority a request's steps move between streams as it moves up the ranks;
+    the result is still bit-identical to the request alone."""
+    with cb.Server(max_active=4, use_graphs=use_graphs, priority=priority) as srv:
         ids, outs = [], []
         for rep in range(2):  # every request twice, so the mix holds more than the slots
             for (geom, levels, iters, st), y in zip(MIX, mix_inputs):
@@ -150,12 +152,13 @@ def test_requests_join_while_another_runs(cb):
         assert i["t_admit"] < ib["t_done"] and i["t_done"] < ib["t_done"]
 
 
-def test_a_failing_request_does_not_disturb_the_others(cb, mix_inputs):
+@pytest.mark.parametrize("priority", ["size", "age"])
+def test_a_failing_request_does_not_disturb_the_others(cb, mix_inputs, priority):
     geom, levels, iters, st = MIX[0]
     y = mix_inputs[0].copy()
     bad = y.copy()
     bad[0, 0, 0] = np.nan
-    with cb.Server(max_active=2) as srv:
+    with cb.Server(max_active=2, priority=priority) as srv:
         o1 = torch.empty(geom.vol_shape, dtype=torch.float32).pin_memory()
         o2 = torch.empty(geom.vol_shape, dtype=torch.float32).pin_memory()
         r_bad = srv.submit(geom, pinned(bad), MU, levels, iters, o1)
@@ -202,3 +205,28 @@ def test_l2_bound_serialises_large_volumes_and_lets_small_ones_pass(cb):
     assert iz["t_admit"] < iy["t_admit"]
     assert stats["bypassed"] >= 1
     assert np.array_equal(outs[0].numpy(), outs[1].numpy())
+
+
+def test_age_priority_finishes_the_oldest_request_first(cb):
+    """Under age priority the oldest admitted request's thread blocks go first: of two equal
+    requests submitted back to back, the first finishes first, and both give the same
+    volume as the request alone."""
+    geom = synth.Geometry(nx=128, ny=128, nz=32, dx=2.0, dy=2.0, dz=2.0, nu=128, nv=48, du=3.0, dv=3.0,
+                          n_views=40)
+    y = synth.random_projections(geom, 11, 0.0, 2.0)
+    with cb.Geometry(geom) as g:
+        ref = cb.reconstruct(g, torch.tensor(y, dtype=torch.float32, device="cuda"), MU, 2, [4, 6]).cpu().numpy()
+    with cb.Server(max_active=4, priority="age") as srv:
+        outs = [torch.empty(geom.vol_shape, dtype=torch.float32).pin_memory() for _ in range(3)]
+        ids = [srv.submit(geom, pinned(y), MU, 2, [4, 6], o) for o in outs]
+        infos = [srv.wait(r, timeout=120) for r in ids]
+        stats = srv.stats()
+    assert stats["completed"] == 3 and stats["max_active_seen"] >= 2
+    assert infos[0]["t_done"] <= infos[1]["t_done"] <= infos[2]["t_done"]
+    for o in outs:
+        assert np.array_equal(o.numpy(), ref)
+
+
+def test_priority_option_is_checked(cb):
+    with pytest.raises(ValueError):
+        cb.Server(priority="fastest")
