@@ -105,17 +105,20 @@ __device__ __forceinline__ void plane_split(const GeomDev &G, const float *s_inv
     above = g * (up ? whi : wlo);
 }
 
-// plane_split for a window on the imager (a <= nv - 1: the row exists).
-__device__ __forceinline__ void plane_split_inside(const float *s_invv, float tc, float2 T, int a, int b, float zp,
-                                                   float ta, float tb, float &g, float &below, float &above)
+// For a window on the imager (a <= nv - 1: the row exists; `in`: row a lies in the window,
+// i.e. b > a): the weighted value of the straddling row times the part of [ta, tb] that
+// lies below the plane z = zp (0 if the window is empty). UP = +1 / -1: the caller knows
+// that a row in the window has v > 0 / v < 0 (its ray rises / falls), so the direction
+// test is dropped; UP = 0 tests it.
+template <int UP>
+__device__ __forceinline__ float plane_below(const float *s_invv, float tc, float2 T, int a, bool in, float zp,
+                                             float ta, float tb)
 {
-    g = b > a ? T.y : 0.0f;
+    const float g = in ? T.y : 0.0f;
     const float iw = s_invv[a];
     const float scl = fminf(fmaxf(tau_zplane(zp, iw, tc), ta), tb);
-    const float wlo = scl - ta, whi = tb - scl;
-    const bool up = iw > 0.0f;
-    below = g * (up ? wlo : whi);
-    above = g * (up ? whi : wlo);
+    const bool up = UP > 0 ? true : UP < 0 ? false : iw > 0.0f;
+    return g * (up ? scl - ta : tb - scl);
 }
 
 // Rows reaching plane zp inside the column lie in the window [a, b) of imager rows (at
@@ -216,42 +219,51 @@ k_backproject(GeomDev G, const float2 *__restrict__ ps, float *__restrict__ out,
                 if (simple && fa_lo >= 0.0f && fb_hi <= (float)(G.nv - 1)) {
                     // every window lies on the imager: no clamping. Slab z receives the rows
                     // strictly between the windows of planes z and z + 1 at weight tb - ta,
-                    // P[a_{z+1}] - P[a_z] - g_z, plus the split parts of both windows' rows.
+                    // P[a_{z+1}] - P[a_z] - g_z, the part of plane z's straddling row above
+                    // the plane, g_z (tb - ta) - below_z, and the part of plane z + 1's
+                    // straddling row below it, below_{z+1}; together
+                    //     (tb - ta) (P[a_{z+1}] - P[a_z]) + below_{z+1} - below_z.
                     // The window of plane zp spans rows v in [zp B, zp A] above z = 0 and
                     // [zp A, zp B] below; a chunk whose planes all lie on one side (all but
-                    // one chunk of a column) fixes that choice for the whole visit.
+                    // one chunk of a column) fixes that choice for the whole visit. Its
+                    // windows' rows then also share the sign of v (below: the test that
+                    // picks the side keeps every window a thousandth of a row pitch or more
+                    // away from v = 0), so the split needs no per-row direction test.
                     auto planes = [&](auto side) {
-                        constexpr int S = decltype(side)::value; // +1 / -1: every plane at z >= 0 / <= 0
+                        constexpr int S = decltype(side)::value; // +1 / -1: every plane at z > 0 / < 0
                         auto bounds = [&](float zsv, float &lo_f, float &hi_f) {
                             const bool pos = S > 0 || (S == 0 && zsv >= 0.0f);
                             lo_f = pos ? B : A;
                             hi_f = pos ? A : B;
                         };
+                        // The window is [a, b) with a = ceil(xa), b = floor(xb) + 1; row a is in it
+                        // iff floor(xb) >= a, i.e. xb >= a (a is an integer), so b is not formed.
                         float lo_f, hi_f;
                         bounds(zs[0], lo_f, hi_f);
                         int a = ceil_small(fmaf(zs[0], lo_f, c0));
-                        int b = floor_small(fmaf(zs[0], hi_f, c1)) + 1;
+                        bool in = fmaf(zs[0], hi_f, c1) >= (float)a;
                         float2 T = __ldg(col + a * G.nu); // (nv + 1) * nu < 2^31: 32-bit offsets
-                        float g, below, above;
-                        plane_split_inside(s_invv, G.tc, T, a, b, zp[0], ta, tb, g, below, above);
-                        acc[0] += above;
-                        float Pprev = T.x, gprev = g;
+                        float Pprev = T.x, bprev = plane_below<S>(s_invv, G.tc, T, a, in, zp[0], ta, tb);
 #pragma unroll
                         for (int z = 0; z < ZC; ++z) {
                             if (z >= nzc) break;
                             bounds(zs[z + 1], lo_f, hi_f);
                             a = ceil_small(fmaf(zs[z + 1], lo_f, c0));
-                            b = floor_small(fmaf(zs[z + 1], hi_f, c1)) + 1;
+                            in = fmaf(zs[z + 1], hi_f, c1) >= (float)a;
                             T = __ldg(col + a * G.nu);
-                            plane_split_inside(s_invv, G.tc, T, a, b, zp[z + 1], ta, tb, g, below, above);
-                            acc[z] = fmaf(wfull, (T.x - Pprev) - gprev, acc[z]) + below;
-                            if (z + 1 < ZC) acc[z + 1] += above; // acc[nzc] is never stored
+                            const float below = plane_below<S>(s_invv, G.tc, T, a, in, zp[z + 1], ta, tb);
+                            acc[z] += fmaf(wfull, T.x - Pprev, below - bprev);
                             Pprev = T.x;
-                            gprev = g;
+                            bprev = below;
                         }
                     };
-                    if (zs[0] >= 0.0f) planes(std::integral_constant<int, 1>());
-                    else if (zs_top <= 0.0f) planes(std::integral_constant<int, -1>());
+                    // Side +1: the window of the lowest plane, hence of every plane, starts
+                    // at a row with v / dv >= zs[0] B - 1e-3 > 0; side -1: every window ends
+                    // at a row with v / dv <= zs_top B + 1e-3 < 0. Otherwise (a chunk that
+                    // meets or nearly meets z = 0) both the side and the direction are
+                    // decided per plane, which gives the same bounds for the planes at z >= 0.
+                    if (zs[0] * B > 2e-3f) planes(std::integral_constant<int, 1>());
+                    else if (zs_top * B < -2e-3f) planes(std::integral_constant<int, -1>());
                     else planes(std::integral_constant<int, 0>());
                 } else if (simple) {
                     // windows may leave the imager: clamped to [0, nv]

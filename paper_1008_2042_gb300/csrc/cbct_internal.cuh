@@ -138,7 +138,7 @@ struct Scalars {
     double beta;     // gamma' / gamma
     double rr;       // ||r||^2 (monitoring)
     double kappa;    // q is stored as kappa * q, kappa = 1 / sqrt(gamma): keeps FP16 in range
-    unsigned int flags; // bit 0: a reduction was not finite; bit 1: a kernel's wait timed out
+    unsigned int flags; // bit 0: a reduction was not finite
     unsigned int pad;
 };
 
@@ -180,22 +180,20 @@ int device_sm_count();
 // Launchers (all asynchronous on `st`; return CBCT_ERR_CUDA on launch failure).
 // Volume element (ix, iy, iz) lives at ix*sx + iy*sy + iz*sz.
 int project_num_blocks(const GeomDev &G);
-// Bytes past the end of a volume that the projector may read (its staging copies round the
-// last z-line up to 16 bytes): every volume buffer passed to launch_project is allocated
-// with at least this much slack, and its base is 16-byte aligned.
+// Bytes past the end of a volume that the projector may read (its 16-byte staging copies
+// round the last z-line up): every volume buffer passed to launch_project is allocated with
+// at least this much slack, and its base is 16-byte aligned.
 constexpr size_t PROJECT_VOLUME_SLACK = 64;
 
 // Dynamic shared memory a projector block may use (opted in per kernel).
 constexpr size_t PROJECT_SMEM_LIMIT = 200 * 1024;
 
 // out holds `storage`-typed values (PM_COUNT: none); y is FP32; sc supplies kappa in
-// PM_Q_SCALED and, when given, receives bit 1 of its flags if a block's wait for its
-// staged lines timed out (that block's results are NaN). With FP32 storage the CGLS modes
-// store |D - S| r and |D - S| q.
+// PM_Q_SCALED. With FP32 storage the CGLS modes store |D - S| r and |D - S| q.
 cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long long sy,
                            long long sz, const float *y, void *out, int mode,
                            double *partials, float count_thr, cudaStream_t st,
-                           int storage = ST_F32, Scalars *sc = nullptr);
+                           int storage = ST_F32, const Scalars *sc = nullptr);
 int backproject_num_blocks(const GeomDev &G);
 // Upper bound of backproject_num_blocks over every grid no larger than G's (any z chunk).
 int backproject_max_blocks(const GeomDev &G);

@@ -155,7 +155,7 @@ cbct_status project_prepare()
 
 cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long long sy,
                            long long sz, const float *y, void *out, int mode,
-                           double *partials, float count_thr, cudaStream_t st, int storage, Scalars *sc)
+                           double *partials, float count_thr, cudaStream_t st, int storage, const Scalars *sc)
 {
     const int threads = proj_threads(G); // 2 rows each
     dim3 grid((unsigned)(G.nviews * G.nu), (unsigned)((G.nv + 2 * threads - 1) / (2 * threads)));

@@ -452,7 +452,6 @@ static cbct_status read_flags(const Work &w, cudaStream_t st)
     cudaError_t e = cudaMemcpyAsync(&flags, &w.sc->flags, sizeof(flags), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return check_cuda(e, "status read-back");
-    if (flags & 2u) return set_error(CBCT_ERR_TIMEOUT, "a projector block timed out waiting for its staged volume lines");
     if (flags & 1u) return set_error(CBCT_ERR_NONFINITE, "an inner product of the iteration was not finite");
     return CBCT_OK;
 }
