@@ -7,6 +7,8 @@ whose device memory is fixed at start-up or a latency-critical loop that cannot 
 the synchronisation an allocation may cause. This file is collected last so that a
 failure here leaves every other test run.
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -65,13 +67,22 @@ def test_project_static_leaves_device_memory_unchanged(cb):
     with cb.Geometry(geom) as g:
         cb.project_static(g, f, out)
         torch.cuda.synchronize()
-        free0, _ = torch.cuda.mem_get_info()
-        alloc0 = torch.cuda.memory_allocated()
-        for _ in range(3):
-            cb.project_static(g, f, out)
-        torch.cuda.synchronize()
-        free1, _ = torch.cuda.mem_get_info()
-        assert torch.cuda.memory_allocated() == alloc0
+        # tensors left unreachable by earlier tests are freed by Python's collector, which
+        # would otherwise run at any moment and move torch's counters: collect them now and
+        # keep the collector off while the calls are measured
+        gc.collect()
+        gc.disable()
+        try:
+            free0, _ = torch.cuda.mem_get_info()
+            alloc0 = torch.cuda.memory_allocated()
+            for _ in range(3):
+                cb.project_static(g, f, out)
+            torch.cuda.synchronize()
+            free1, _ = torch.cuda.mem_get_info()
+            alloc1 = torch.cuda.memory_allocated()
+        finally:
+            gc.enable()
+        assert alloc1 == alloc0, (alloc0, alloc1)
         assert free1 == free0, (free0, free1)
 
 
