@@ -223,7 +223,9 @@ cbct_status cbct_cgls(const cbct_geometry *geom, const float *y, float *x, int n
  * y: device [n_views][nv][nu]; f_out: device [nz][ny][nx] (finest grid).
  * Uses the geometry's reconstruction workspace (allocated on first use; its size is
  * cbct_reconstruct_workspace_size). Synchronises the stream at the end.
- * Errors: INVALID_ARG, UNSUPPORTED, OUT_OF_MEMORY, CUDA, NONFINITE.
+ * Errors: INVALID_ARG, UNSUPPORTED, OUT_OF_MEMORY, CUDA, NONFINITE; TIMEOUT if a
+ * projector block's bounded wait for its precomputed ray trace ran out (its rows are then
+ * NaN).
  */
 cbct_status cbct_reconstruct(const float *y, const cbct_geometry *geom, float mu,
                              float lambda, int levels, const int *iters, float *f_out,

@@ -13,7 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcbcttf.so")
 SOURCES = ["geometry.cu", "project.cu", "project_groups_16_32.cu", "project_groups_40_56.cu",
-           "project_groups_64_96.cu", "backproject.cu", "tf.cu", "recon.cu", "project_static.cu", "serve.cu"]
+           "project_groups_64_96.cu", "project_trace.cu", "backproject.cu", "tf.cu", "recon.cu", "project_static.cu",
+           "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

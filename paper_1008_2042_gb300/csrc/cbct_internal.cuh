@@ -138,7 +138,7 @@ struct Scalars {
     double beta;     // gamma' / gamma
     double rr;       // ||r||^2 (monitoring)
     double kappa;    // q is stored as kappa * q, kappa = 1 / sqrt(gamma): keeps FP16 in range
-    unsigned int flags; // bit 0: a reduction was not finite
+    unsigned int flags; // bit 0: a reduction was not finite; bit 1: a projector block's wait timed out
     unsigned int pad;
 };
 
@@ -189,11 +189,20 @@ constexpr size_t PROJECT_VOLUME_SLACK = 64;
 constexpr size_t PROJECT_SMEM_LIMIT = 200 * 1024;
 
 // out holds `storage`-typed values (PM_COUNT: none); y is FP32; sc supplies kappa in
-// PM_Q_SCALED. With FP32 storage the CGLS modes store |D - S| r and |D - S| q.
+// PM_Q_SCALED and, when given, receives bit 1 of its flags if a block's wait for its trace
+// record timed out (that block's rows are NaN). With FP32 storage the CGLS modes store
+// |D - S| r and |D - S| q. traces: the grid's trace table from launch_trace_table built with
+// the same sx, sy (the projector then copies each column's phase 1 instead of computing
+// it), or nullptr.
 cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long long sy,
                            long long sz, const float *y, void *out, int mode,
                            double *partials, float count_thr, cudaStream_t st,
-                           int storage = ST_F32, const Scalars *sc = nullptr);
+                           int storage = ST_F32, Scalars *sc = nullptr, const void *traces = nullptr);
+// The projector's trace table of a grid (trace_table_bytes(G) bytes, 16-byte aligned):
+// phase 1 of every (view, imager column), column offsets for the strides sx, sy.
+size_t trace_table_bytes(const GeomDev &G);
+cbct_status launch_trace_table(const GeomDev &G, long long sx, long long sy, void *tab, cudaStream_t st);
+cbct_status trace_table_prepare();
 int backproject_num_blocks(const GeomDev &G);
 // Upper bound of backproject_num_blocks over every grid no larger than G's (any z chunk).
 int backproject_max_blocks(const GeomDev &G);
@@ -238,6 +247,7 @@ struct cbct_geometry {
 };
 
 namespace cbct {
+constexpr int MAX_LEVELS = 8; // multigrid levels a reconstruction may use
 GeomDev level_geom(const cbct_geometry *g, int level);
 cbct_status ensure_scratch(cbct_geometry *g, size_t bytes);
 

@@ -142,6 +142,8 @@ cbct_status project_group_of(const GeomDev &G, int *sg) { return choose_group(G,
 
 cbct_status project_prepare()
 {
+    cbct_status t = trace_table_prepare();
+    if (t != CBCT_OK) return t;
     for (int i = 0; i < PROJECT_N_GROUP_SIZES; ++i)
         for (int mode = PM_PLAIN; mode <= PM_COUNT; ++mode)
             for (int storage = ST_F32; storage <= ST_F16; ++storage) {
@@ -155,7 +157,8 @@ cbct_status project_prepare()
 
 cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long long sy,
                            long long sz, const float *y, void *out, int mode,
-                           double *partials, float count_thr, cudaStream_t st, int storage, const Scalars *sc)
+                           double *partials, float count_thr, cudaStream_t st, int storage, Scalars *sc,
+                           const void *traces)
 {
     const int threads = proj_threads(G); // 2 rows each
     dim3 grid((unsigned)(G.nviews * G.nu), (unsigned)((G.nv + 2 * threads - 1) / (2 * threads)));
@@ -172,7 +175,9 @@ cbct_status launch_project(const GeomDev &G, const float *f, long long sx, long 
     const size_t smem = project_smem(G, sg);
     GeomDev g = G;
     int isx = (int)sx, isy = (int)sy;
-    void *args[] = {&g, &f, &isx, &isy, &y, &out, &partials, &count_thr, &sc};
+    const int4 *tr = mode == PM_COUNT ? nullptr : reinterpret_cast<const int4 *>(traces);
+    int tcap = trace_cap(G);
+    void *args[] = {&g, &f, &isx, &isy, &y, &out, &partials, &count_thr, &sc, &tr, &tcap};
     ProfToken tok = prof_start(CBCT_KERNEL_PROJECT, st);
     cudaError_t e = cudaLaunchKernel(fn, grid, dim3((unsigned)threads), args, smem, st);
     prof_stop(tok, st);

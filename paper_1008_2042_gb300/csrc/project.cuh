@@ -58,6 +58,14 @@ static inline size_t project_smem(const GeomDev &G, int sg)
            sizeof(float) * (line_region(G, sg) + (size_t)G.nz * (sg + 1) + 2 * (size_t)G.nz);
 }
 
+// The trace table (k_trace_table): a record of 16 + 8 trace_cap bytes per (view, imager
+// column), trace_cap = nx + ny + 2 rounded up to 4.
+static inline int trace_cap(const GeomDev &G) { return ((G.nx + G.ny + 2 + 3) / 4) * 4; }
+static inline size_t trace_smem(const GeomDev &G)
+{
+    return sizeof(float) * (2 * (size_t)trace_cap(G) + 4 * (PROJ_THREADS / 32) + (size_t)G.nx + G.ny + 2);
+}
+
 // Column segments per group (one staged set of z-lines and one prefix table); the
 // dispatcher (project.cu) picks one per launch from an estimate of its per-group cost and
 // of the blocks it keeps resident.

@@ -34,55 +34,84 @@ __device__ __forceinline__ void cp_async16(float *smem_dst, const float *gsrc)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// One block per (view, imager column, chunk of rows), volume z-contiguous (sz = 1).
-// Phase 1 (whole block): the transverse Siddon trace of the column's rays — the
-// crossings with the x planes and with the y planes are each increasing in tau, so every
-// crossing's position in the merged order is its own index plus the number of crossings
-// of the other family before it (binary search); this yields the list of (x, y) voxel
-// columns the rays visit and the tau at which each is left. For every segment the block
-// also stores its length and where its column's z-line will sit in shared memory.
-// Phase 2, per group of SG segments: the block stages the group's z-lines and builds
-// the per-slab prefix table T[k][u] over the group's columns; then each thread (two
-// imager rows) adds, for each run of whole columns a row spends in one z slab, the
-// table difference, and splits exactly each column in which the row crosses a z plane.
-template <int MODE, typename TP, int SG>
-__global__ void __launch_bounds__(PROJ_THREADS, CBCT_PROJ_MIN_BLOCKS)
-k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *__restrict__ y,
-          TP *__restrict__ out, double *__restrict__ partials, float count_thr, const Scalars *__restrict__ sc)
+// One-shot bulk (TMA) copy of a block's trace record into shared memory, completed on an
+// mbarrier that one thread initialises, arms, feeds and waits on (the others wait at the
+// block barrier that follows, so no warp spins).
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
 {
-    extern __shared__ __align__(16) float smem[];
-    __shared__ double s_warp[PROJ_THREADS / 32];
-    const int cap = ((G.nx + G.ny + 2 + SG - 1) / SG) * SG;
-    float *sEnd = smem;                                    // tau at which segment j ends
-    int *sCol = reinterpret_cast<int *>(sEnd + cap);      // voxel-column offset of segment j
-    float2 *sSeg = reinterpret_cast<float2 *>(sCol + cap); // (line offset bits, length) of segment j
-    const int pitch = ((G.nz + 6 + 3) / 4) * 4;            // floats per staged line
-    const int quads = pitch / 4;                           // 16-byte pieces per line slot
-    float *sLine = reinterpret_cast<float *>(sSeg + cap);  // the staged z-lines of one group
-    float *sA = sLine;                                     // phase 1: x-plane crossings, in ray order
-    float *sB = sA + (G.nx + 1);                           // phase 1: y-plane crossings
-    const int lregion = max(SG * pitch, ((G.nx + G.ny + 2 + 3) / 4) * 4);
-    constexpr int TPITCH = SG + 1;                         // odd: the build's threads (slabs) hit distinct banks
-    float *sTab = sLine + lregion;                         // [nz][SG + 1] per-slab prefix table
-    float *sBase = sTab + G.nz * TPITCH;                   // [2][nz] running per-slab totals
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// global -> shared bulk copy of `bytes` (a multiple of 16) between 16-byte-aligned addresses,
+// marked evict-first in L2: each record is read once per projection, and the volume lines
+// and the stack the projector and the next kernels reuse should stay
+__device__ __forceinline__ void bulk_copy_g2s(void *smem_dst, const void *gsrc, unsigned bytes, unsigned long long *bar)
+{
+    unsigned long long policy;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(policy));
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;\n" ::"r"(
+            smem_u32(smem_dst)),
+        "l"(gsrc), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+// tries of the record wait before a block gives up (each try may suspend the thread for a
+// while; together well over a second): a copy that never lands ends the block with NaN
+// results and bit 1 of the iteration's status word instead of a hang
+constexpr int PROJ_WAIT_TRIES = 1 << 22;
 
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int view = blockIdx.x / G.nu;
-    const int iu = blockIdx.x - view * G.nu;
-
-    // ---- transverse ray, shared by every row ----
+// The transverse ray shared by every row of imager column iu in a view, and the tau
+// interval in which it crosses the volume's (x, y) footprint.
+struct ColumnRay {
+    float dxr, dyr, qx, qy, inv_x, inv_y, tau_in, tau_out;
+    int sxs, sys;
+    bool hit;
+};
+__device__ __forceinline__ ColumnRay column_ray(const GeomDev &G, int view, int iu)
+{
+    ColumnRay c;
     const float2 cs = G.cs[view];
-    float dxr, dyr, qx, qy;
-    ray_xy(G, cs.x, cs.y, imager_u(G, iu), dxr, dyr, qx, qy);
-    const float inv_x = safe_rcp(dxr), inv_y = safe_rcp(dyr);
-    const float xa = tau_plane(G.x0, qx, inv_x), xb = tau_plane(plane_at(G.nx, G.dx, G.x0), qx, inv_x);
-    const float ya = tau_plane(G.y0, qy, inv_y), yb = tau_plane(plane_at(G.ny, G.dy, G.y0), qy, inv_y);
-    const float tau_in = fmaxf(fmaxf(fminf(xa, xb), fminf(ya, yb)), -G.tc);
-    const float tau_out = fminf(fminf(fmaxf(xa, xb), fmaxf(ya, yb)), 1.0f - G.tc);
-    const bool hit = tau_in < tau_out;
-    const int sxs = dxr > 0.0f ? 1 : -1, sys = dyr > 0.0f ? 1 : -1;
+    ray_xy(G, cs.x, cs.y, imager_u(G, iu), c.dxr, c.dyr, c.qx, c.qy);
+    c.inv_x = safe_rcp(c.dxr);
+    c.inv_y = safe_rcp(c.dyr);
+    const float xa = tau_plane(G.x0, c.qx, c.inv_x), xb = tau_plane(plane_at(G.nx, G.dx, G.x0), c.qx, c.inv_x);
+    const float ya = tau_plane(G.y0, c.qy, c.inv_y), yb = tau_plane(plane_at(G.ny, G.dy, G.y0), c.qy, c.inv_y);
+    c.tau_in = fmaxf(fmaxf(fminf(xa, xb), fminf(ya, yb)), -G.tc);
+    c.tau_out = fminf(fminf(fmaxf(xa, xb), fmaxf(ya, yb)), 1.0f - G.tc);
+    c.hit = c.tau_in < c.tau_out;
+    c.sxs = c.dxr > 0.0f ? 1 : -1;
+    c.sys = c.dyr > 0.0f ? 1 : -1;
+    return c;
+}
 
-    // ---- phase 1: crossings of each plane family, then their merged order ----
+// Phase 1 of a column (whole block, one barrier inside): the crossings of the ray with
+// each plane family are increasing in tau, so every crossing's position in the merged order
+// is its own index plus the number of crossings of the other family before it. Writes, for
+// the nseg = nA + nB + 1 segments the ray spends in (x, y) voxel columns, sEnd[j] (the tau at
+// which segment j ends) and sCol[j] (its column's offset ix * sx + iy * sy); sA (nx + 1
+// floats), sB (ny + 1) and s_cnt (4 per warp) are scratch. Returns (nA, nB, ix_e, iy_e): the
+// x- and y-plane crossings inside the volume and the column entered first.
+__device__ __forceinline__ int4 trace_column(const GeomDev &G, const ColumnRay &ray, int sx, int sy, float *sA,
+                                             float *sB, unsigned *s_cnt, float *sEnd, int *sCol, int tid, int nthr)
+{
+    const float dxr = ray.dxr, dyr = ray.dyr, qx = ray.qx, qy = ray.qy, inv_x = ray.inv_x, inv_y = ray.inv_y;
+    const float tau_in = ray.tau_in, tau_out = ray.tau_out;
+    const bool hit = ray.hit;
+    const int sxs = ray.sxs, sys = ray.sys;
     // counts of the crossings before the entry point and inside the volume: per thread, then
     // one block-wide sum (the lists are written before the barrier of that sum)
     unsigned cnt4[4] = {0u, 0u, 0u, 0u}; // a_le, a_in, b_le, b_in
@@ -102,8 +131,7 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
             cnt4[3] += t > tau_in && t < tau_out;
         }
     }
-    // per-warp sums, parked in the segment records (written only after the merge below)
-    unsigned *s_cnt = reinterpret_cast<unsigned *>(sSeg);
+    // per-warp sums
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const unsigned v = __reduce_add_sync(0xffffffffu, cnt4[q]);
@@ -160,11 +188,87 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
         sEnd[r] = t;
         sCol[r + 1] = cx * sx + cy * sy;
     }
-    const int col0 = ix_e * sx + iy_e * sy;
     if (tid == 0) {
-        sCol[0] = col0;
+        sCol[0] = ix_e * sx + iy_e * sy;
         sEnd[nseg - 1] = tau_out;
     }
+    return make_int4(nA, nB, ix_e, iy_e);
+}
+
+
+// One block per (view, imager column, chunk of rows), volume z-contiguous (sz = 1).
+// Phase 1 (whole block): the transverse Siddon trace of the column's rays — the
+// crossings with the x planes and with the y planes are each increasing in tau, so every
+// crossing's position in the merged order is its own index plus the number of crossings
+// of the other family before it (binary search); this yields the list of (x, y) voxel
+// columns the rays visit and the tau at which each is left. For every segment the block
+// also stores its length and where its column's z-line will sit in shared memory.
+// Phase 2, per group of SG segments: the block stages the group's z-lines and builds
+// the per-slab prefix table T[k][u] over the group's columns; then each thread (two
+// imager rows) adds, for each run of whole columns a row spends in one z slab, the
+// table difference, and splits exactly each column in which the row crosses a z plane.
+template <int MODE, typename TP, int SG>
+__global__ void __launch_bounds__(PROJ_THREADS, CBCT_PROJ_MIN_BLOCKS)
+k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *__restrict__ y,
+          TP *__restrict__ out, double *__restrict__ partials, float count_thr, Scalars *__restrict__ sc,
+          const int4 *__restrict__ traces, int trace_cap)
+{
+    extern __shared__ __align__(16) float smem[];
+    __shared__ double s_warp[PROJ_THREADS / 32];
+    __shared__ __align__(8) unsigned long long s_bar; // completion of the trace record's copy
+    const int cap = ((G.nx + G.ny + 2 + SG - 1) / SG) * SG;
+    float *sEnd = smem;                                    // tau at which segment j ends
+    int *sCol = reinterpret_cast<int *>(sEnd + cap);      // voxel-column offset of segment j
+    float2 *sSeg = reinterpret_cast<float2 *>(sCol + cap); // (line offset bits, length) of segment j
+    const int pitch = ((G.nz + 6 + 3) / 4) * 4;            // floats per staged line
+    const int quads = pitch / 4;                           // 16-byte pieces per line slot
+    float *sLine = reinterpret_cast<float *>(sSeg + cap);  // the staged z-lines of one group
+    float *sA = sLine;                                     // phase 1: x-plane crossings, in ray order
+    float *sB = sA + (G.nx + 1);                           // phase 1: y-plane crossings
+    const int lregion = max(SG * pitch, ((G.nx + G.ny + 2 + 3) / 4) * 4);
+    constexpr int TPITCH = SG + 1;                         // odd: the build's threads (slabs) hit distinct banks
+    float *sTab = sLine + lregion;                         // [nz][SG + 1] per-slab prefix table
+    float *sBase = sTab + G.nz * TPITCH;                   // [2][nz] running per-slab totals
+
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int view = blockIdx.x / G.nu;
+    const int iu = blockIdx.x - view * G.nu;
+
+    // ---- transverse ray, shared by every row ----
+    const ColumnRay ray = column_ray(G, view, iu);
+    const float dxr = ray.dxr, dyr = ray.dyr, qx = ray.qx, qy = ray.qy;
+    const float tau_in = ray.tau_in, tau_out = ray.tau_out;
+    const bool hit = ray.hit;
+    const int sxs = ray.sxs, sys = ray.sys;
+
+    // ---- phase 1: crossings of each plane family, then their merged order ----
+    int4 tr;
+    bool timed_out = false;
+    if (traces && hit) {
+        // phase 1 from the grid's trace table: the record's segment lists by one bulk copy
+        const int4 *rec = traces + (size_t)blockIdx.x * (1 + trace_cap / 2);
+        tr = __ldg(rec);
+        int bad = 0;
+        if (tid == 0) {
+            const unsigned bytes = 4u * (unsigned)((tr.x + tr.y + 1 + 3) & ~3);
+            mbar_init(&s_bar, 1u);
+            mbar_arrive_expect_tx(&s_bar, 2u * bytes);
+            bulk_copy_g2s(sEnd, rec + 1, bytes, &s_bar);
+            bulk_copy_g2s(sCol, reinterpret_cast<const float *>(rec + 1) + trace_cap, bytes, &s_bar);
+            bool landed = false;
+            for (int it = 0; it < PROJ_WAIT_TRIES && !(landed = mbar_try_wait(&s_bar, 0u)); ++it) {
+            }
+            bad = !landed;
+        }
+        timed_out = __syncthreads_or(bad) != 0;
+        if (timed_out && sc && tid == 0) atomicOr(&sc->flags, 2u);
+    } else {
+        // per-warp sums of phase 1 are parked in the segment records (written after it)
+        tr = trace_column(G, ray, sx, sy, sA, sB, reinterpret_cast<unsigned *>(sSeg), sEnd, sCol, tid, nthr);
+    }
+    const int nA = tr.x, nB = tr.y, ix_e = tr.z, iy_e = tr.w, nseg = nA + nB + 1;
+    const int col0 = ix_e * sx + iy_e * sy;
+    const float inv_dx = 1.0f / G.dx, inv_dy = 1.0f / G.dy;
     for (int q = nseg + tid; q < cap; q += nthr) { // zero-length padding up to whole groups
         sEnd[q] = tau_out;
         sCol[q] = col0;
@@ -191,7 +295,7 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
         inv_v[r] = v != 0.0f ? __frcp_rn(v) : 1e30f;
         skz[r] = v >= 0.0f ? 1 : -1;
         kz[r] = (int)floorf((v * (G.tc + tau_in) - G.z0) / G.dz);
-        active[r] = hit && ok[r] && kz[r] >= 0 && kz[r] < G.nz;
+        active[r] = hit && !timed_out && ok[r] && kz[r] >= 0 && kz[r] < G.nz;
         tzn[r] = active[r] ? tau_zplane(plane_at(kz[r] + (skz[r] > 0), G.dz, G.z0), inv_v[r], G.tc) : P_INF;
         if (active[r] && tzn[r] <= tau_in) { // the entry point already lies past that plane
             kz[r] += skz[r];
@@ -222,7 +326,7 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
                 s0 = e;
             }
         }
-    } else if (hit) {
+    } else if (hit && !timed_out) {
         // Per group of SG segments: stage the z-lines of its columns (16-byte cp.async into
         // one buffer: a second buffer to copy the next group ahead would cost a resident
         // block, which hides more latency than the early copy), build once for the block the
@@ -356,6 +460,10 @@ k_project(GeomDev G, const float *__restrict__ f, int sx, int sy, const float *_
     }
 
     // ---- epilogue ----
+    if (timed_out) { // the trace record never arrived: NaN rows, reported through sc
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = __int_as_float(0x7fc00000);
+    }
     double red = 0.0;
     const float kappa = (MODE == PM_Q_SCALED) ? (float)sc->kappa : 1.0f;
     constexpr bool PRESCALE = sizeof(TP) == 4;

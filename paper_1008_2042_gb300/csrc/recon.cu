@@ -336,6 +336,7 @@ struct Work {
     float *X, *X2, *P, *S, *Fa, *Fb; // X, X2: the CGLS iterate and the next momentum point
     void *R, *Q; // residual and projected search direction: n_views*nv*nu values of the storage type
     float2 *PS; // row prefix sums of the prescaled residual, input of the adjoint
+    void *TR[MAX_LEVELS]; // per level: the projector's trace table (internal layout strides)
     double *partials;
     Scalars *sc;
 };
@@ -368,9 +369,14 @@ static size_t work_layout(const cbct_geometry *g, char *base, Work *w)
     float *Fa = (float *)take(VB), *Fb = (float *)take(VB);
     void *R = take(4 * M), *Q = take(4 * M); // sized for FP32, the widest storage type
     float2 *PS = (float2 *)take(sizeof(float2) * prefix_elems(d));
+    void *TR[MAX_LEVELS];
+    for (int lev = 0; lev < MAX_LEVELS; ++lev) TR[lev] = take(trace_table_bytes(level_geom(g, lev)));
     double *partials = (double *)take(sizeof(double) * max_partials(g));
     Scalars *sc = (Scalars *)take(sizeof(Scalars));
-    if (w) *w = Work{X, X2, P, S, Fa, Fb, R, Q, PS, partials, sc};
+    if (w) {
+        *w = Work{X, X2, P, S, Fa, Fb, R, Q, PS, {}, partials, sc};
+        for (int lev = 0; lev < MAX_LEVELS; ++lev) w->TR[lev] = TR[lev];
+    }
     return off;
 }
 
@@ -410,7 +416,7 @@ static cbct_status get_work(cbct_geometry *g, void *ws, size_t ws_bytes, Work *w
     } while (0)
 
 static cbct_status run_cgls(const GeomDev &G, const float *y, float *x, int n_iter, const Work &w, int storage,
-                            cudaStream_t st)
+                            const void *traces, cudaStream_t st)
 {
     const long long sz = 1, sx = G.nz, sy = (long long)G.nx * G.nz;
     const size_t N = (size_t)G.nx * G.ny * G.nz, M = (size_t)G.nviews * G.nv * G.nu;
@@ -420,14 +426,15 @@ static cbct_status run_cgls(const GeomDev &G, const float *y, float *x, int n_it
     const int prescale = storage == ST_F32 ? 0 : 1;
     const int scale_q = storage == ST_F16 ? 1 : 0;
     // r = y - P x; s = P^T r; p = s; gamma = ||s||^2
-    TRY(launch_project(G, x, sx, sy, sz, y, w.R, PM_RESID, w.partials, 0.0f, st, storage, w.sc));
+    TRY(launch_project(G, x, sx, sy, sz, y, w.R, PM_RESID, w.partials, 0.0f, st, storage, w.sc, traces));
     TRY(finalize(w.partials, nbp, w.sc, FIN_RR, st));
     TRY(launch_row_prefix(G, w.R, w.PS, prescale, st, storage));
     TRY(launch_backproject(G, w.PS, w.S, sx, sy, sz, w.P, w.partials, st));
     TRY(finalize(w.partials, nbb, w.sc, FIN_GAMMA, st, scale_q));
     for (int l = 0; l < n_iter; ++l) {
         // q = P p, alpha = gamma / ||q||^2
-        TRY(launch_project(G, w.P, sx, sy, sz, nullptr, w.Q, PM_Q_SCALED, w.partials, 0.0f, st, storage, w.sc));
+        TRY(launch_project(G, w.P, sx, sy, sz, nullptr, w.Q, PM_Q_SCALED, w.partials, 0.0f, st, storage, w.sc,
+                           traces));
         TRY(finalize(w.partials, nbp, w.sc, FIN_ALPHA, st));
         if (l == n_iter - 1) { // last update: x only; s and p would not be used again
             CBCT_TIMED(CBCT_KERNEL_OTHER, st, k_update_xp<<<vec_blocks(N), 256, 0, st>>>(x, w.P, w.S, w.sc, N, 0));
@@ -452,6 +459,7 @@ static cbct_status read_flags(const Work &w, cudaStream_t st)
     cudaError_t e = cudaMemcpyAsync(&flags, &w.sc->flags, sizeof(flags), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return check_cuda(e, "status read-back");
+    if (flags & 2u) return set_error(CBCT_ERR_TIMEOUT, "a projector block timed out waiting for its trace record");
     if (flags & 1u) return set_error(CBCT_ERR_NONFINITE, "an inner product of the iteration was not finite");
     return CBCT_OK;
 }
@@ -471,9 +479,10 @@ static cbct_status reset_scalars(const Work &w, cudaStream_t st)
 // level's last iteration); t is advanced to t^(k+1). Internal layout: axis 0 = z,
 // axis 1 = x, axis 2 = y.
 static cbct_status run_a2_iteration(const GeomDev &G, const float *y, float mu, bool last, const cbct_recon_opts &o,
-                                    Work &w, double &t, float **f_cur, float **f_other, cudaStream_t st)
+                                    Work &w, const void *traces, double &t, float **f_cur, float **f_other,
+                                    cudaStream_t st)
 {
-    TRY(run_cgls(G, y, w.X, o.n_cgls, w, o.storage, st));
+    TRY(run_cgls(G, y, w.X, o.n_cgls, w, o.storage, traces, st));
     const double t_next = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
     const float c = o.momentum ? (float)((t - 1.0) / t_next) : 0.0f;
     TRY(launch_tf_shrink_fused(G.nz, G.nx, G.ny, w.X, mu, o.positivity, *f_other, *f_cur, c, last ? nullptr : w.X2,
@@ -532,6 +541,12 @@ cbct_status reconstruct_cursor_step(ReconCursor *c, cudaStream_t st)
     Work &w = c->w;
     if (!c->started) {
         TRY(reset_scalars(w, st));
+        // the projector's trace table of every level, once per reconstruction (the iteration's
+        // volumes are z-contiguous: strides nz and nx nz)
+        for (int lev = 0; lev < c->levels; ++lev) {
+            const GeomDev G = level_geom(c->g, lev);
+            TRY(launch_trace_table(G, G.nz, (long long)G.nx * G.nz, w.TR[lev], st));
+        }
         c->f_cur = w.Fa;
         c->f_other = w.Fb;
         c->lev = c->levels - 1;
@@ -565,7 +580,8 @@ cbct_status reconstruct_cursor_step(ReconCursor *c, cudaStream_t st)
         }
         const bool had_iteration = c->k < iters;
         if (had_iteration) {
-            TRY(run_a2_iteration(G, c->y, c->mu, c->k + 1 == iters, c->o, w, c->t, &c->f_cur, &c->f_other, st));
+            TRY(run_a2_iteration(G, c->y, c->mu, c->k + 1 == iters, c->o, w, w.TR[c->lev], c->t, &c->f_cur,
+                                 &c->f_other, st));
             c->k++;
         }
         if (c->k >= iters) { // level done: the next one starts with the prolongation
@@ -632,12 +648,15 @@ extern "C" cbct_status cbct_project_ex(const cbct_geometry *gc, const float *f, 
     cbct_geometry *g = const_cast<cbct_geometry *>(gc);
     const GeomDev G = level_geom(g, 0);
     const size_t N = (size_t)G.nx * G.ny * G.nz;
-    TRY(ensure_scratch(g, sizeof(float) * N + PROJECT_VOLUME_SLACK));
+    const size_t vol_bytes = align256(sizeof(float) * N + PROJECT_VOLUME_SLACK);
+    TRY(ensure_scratch(g, vol_bytes + trace_table_bytes(G)));
     cudaStream_t st = (cudaStream_t)stream;
     float *fz = g->d_scratch;
+    void *traces = reinterpret_cast<char *>(g->d_scratch) + vol_bytes;
     TRY(transpose(f, fz, G.nx, G.ny, G.nz, true, st));
+    TRY(launch_trace_table(G, G.nz, (long long)G.nx * G.nz, traces, st));
     return launch_project(G, fz, G.nz, (long long)G.nx * G.nz, 1, nullptr, g_out, PM_PLAIN, nullptr, 0.0f, st,
-                          (int)g_type);
+                          (int)g_type, nullptr, traces);
 }
 
 extern "C" cbct_status cbct_project(const cbct_geometry *gc, const float *f, float *g_out, cbct_stream_t stream)
@@ -714,7 +733,8 @@ cbct_status validate_recon_args(float mu, float lambda, int levels, const int *i
     if (!std::isfinite(lambda)) return set_error(CBCT_ERR_INVALID_ARG, "reconstruct: lambda must be finite");
     if (lambda != 0.0f)
         return set_error(CBCT_ERR_UNSUPPORTED, "reconstruct: lambda must be 0 (the method's only parameter is mu)");
-    if (levels < 1 || levels > 8) return set_error(CBCT_ERR_INVALID_ARG, "reconstruct: levels must be in 1..8");
+    if (levels < 1 || levels > MAX_LEVELS)
+        return set_error(CBCT_ERR_INVALID_ARG, "reconstruct: levels must be in 1..%d", MAX_LEVELS);
     for (int i = 0; i < levels; ++i)
         if (iters[i] < 0 || iters[i] > 100000) return set_error(CBCT_ERR_INVALID_ARG, "reconstruct: bad iteration count");
     if (o.n_cgls < 1 || o.n_cgls > 1000) return set_error(CBCT_ERR_INVALID_ARG, "reconstruct: n_cgls must be in 1..1000");
@@ -762,7 +782,8 @@ extern "C" cbct_status cbct_cgls(const cbct_geometry *gc, const float *y, float 
     TRY(reset_scalars(w, st));
     const GeomDev G = level_geom(g, 0);
     TRY(transpose(x, w.Fa, G.nx, G.ny, G.nz, true, st));
-    if (n_iter > 0) TRY(run_cgls(G, y, w.Fa, n_iter, w, ST_F32, st));
+    TRY(launch_trace_table(G, G.nz, (long long)G.nx * G.nz, w.TR[0], st));
+    if (n_iter > 0) TRY(run_cgls(G, y, w.Fa, n_iter, w, ST_F32, w.TR[0], st));
     TRY(transpose(w.Fa, x, G.nx, G.ny, G.nz, false, st));
     return read_flags(w, st);
 }

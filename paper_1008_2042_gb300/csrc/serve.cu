@@ -355,6 +355,9 @@ void worker_main(cbct_server *srv)
             if (e != cudaSuccess) {
                 status = check_cuda(e, "server: request work");
                 msg = cbct_last_error();
+            } else if (*srv->slot_flags(r->slot) & 2u) {
+                status = CBCT_ERR_TIMEOUT;
+                msg = "a projector block timed out waiting for its trace record";
             } else if (*srv->slot_flags(r->slot) & 1u) {
                 status = CBCT_ERR_NONFINITE;
                 msg = "an inner product of the iteration was not finite";
