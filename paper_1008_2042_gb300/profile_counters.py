@@ -32,7 +32,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 
 KERNEL_SOURCES = {
-    "k_project": ("project.cu", "project.cuh", "project_kernel.cuh"),
+    "k_project": ("project.cu", "project.cuh", "project_kernel.cuh", "project_trace.cu"),
     "k_backproject": ("backproject.cu",),
 }
 OPS = {"k_project": "project", "k_backproject": "backproject"}
