@@ -110,7 +110,11 @@ cbct_status cbct_geometry_destroy(cbct_geometry *geom);
  * Forward projection g = P f (Eq. (1); Section 2.2.1: one ray per pixel, Siddon's exact
  * ray tracing): g_i = sum_j a_ij f_j, a_ij = length (mm) of ray i inside voxel j.
  * f: device [nz][ny][nx]; g: device [n_views][nv][nu]. FP32 arithmetic.
- * Uses the geometry's scratch (allocated on first use: one volume).
+ * Uses the geometry's scratch (allocated on first use, grown when too small): the volume in
+ * the projector's z-fastest layout and the grid's ray-trace table, 16 + 8 (nx + ny + 2)
+ * bytes per (view, imager column). Every projection block copies its trace record with a
+ * bounded wait; should that wait ever run out, the block's rows are written as NaN (the
+ * call itself cannot see it; cbct_reconstruct reports it as TIMEOUT).
  */
 cbct_status cbct_project(const cbct_geometry *geom, const float *f, float *g,
                          cbct_stream_t stream);
