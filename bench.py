@@ -300,7 +300,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic torso phantom (30 ellipsoids), uniform random projections",
-        "config": workload_config(geom, iters, {"sample": sample}),
+        "config": workload_config(geom, iters, {"sample": sample,
+                                                "l2": "not applicable: the FP64 oracle runs on the host cores"}),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
